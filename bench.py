@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark of the Lloyd step on GB300: point-centroid distance evaluations
+per second per Lloyd iteration (N * K per step).
+
+One step = one pass of the whole hot path over the points resident in HBM:
+the fused reassignment + per-block sums kernel, then the fixed-order
+reduction / divide / error kernel.  Default workload: N = 1e8 float32 points
+in 3-D from 32 anisotropic Gaussians, K = 32, k-means++ start (synthetic,
+seeded).  The points (1.2 GB) exceed the 129 MB L2, so no flush is needed
+between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (a bounded sample of the same workload per
+step).  Under torchrun each rank runs an independent replica (the path needs
+no cross-GPU exchange for replicas; value = all ranks' evaluations / max time).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "point-centroid distance evals/s per Lloyd iter"
+UNIT = "evals/s"
+FP32_LANES_PER_SM = 128  # FFMA lanes per SM per clock (2 flops each)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain_3d_n1e8_k32")
+    ap.add_argument("--n", type=int, default=0, help="override N (smaller runs, profiling)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_workload(name, n_override):
+    import synth
+    kw = {}
+    if n_override:
+        kw["n"] = n_override
+    return synth.workload(name, **kw)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read-only queries)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("km_assign.cu", "km_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2405_12052_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, n, k, d):
+    """DRAM bytes per launch of the assign kernel from the committed ncu
+    summary, if it was taken on the current source (else None)."""
+    p = os.path.join(ROOT, "profiles", "assign_fast_traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p))
+    if rec.get("source_sha") != source_hash():
+        return None
+    if rec.get("d") != d or rec.get("k") != k:
+        return None
+    # captured on a smaller N: traffic grows in proportion to the points streamed
+    return rec["dram_bytes_per_launch"] * (n / rec["n"])
+
+
+def cpu_baseline(w, seconds):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded sample:
+    the first n_s points of the same (shuffled) workload."""
+    import numpy as np
+    import oracle
+    orc = oracle.default()
+    x = w["x"]
+    n = x.shape[1]
+    k = w["k"]
+    ns = min(n, 1 << 18)
+    xs = np.ascontiguousarray(x[:, :ns])
+    t0 = time.perf_counter()
+    orc.step(xs, w["mu0"])
+    t1 = time.perf_counter() - t0
+    target = max(1.0, seconds / 3)
+    ns = int(min(n, max(ns, ns * target / max(t1, 1e-3))))
+    xs = np.ascontiguousarray(x[:, :ns])
+    times = []
+    t_end = time.perf_counter() + seconds
+    while len(times) < 3 or (time.perf_counter() < t_end and len(times) < 10):
+        t0 = time.perf_counter()
+        orc.step(xs, w["mu0"])
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end and len(times) >= 1:
+            break
+    ts = statistics.median(times)
+    return {"value": ns * k / ts, "unit": UNIT, "cores": orc.threads(), "kind": "oracle",
+            "sample": f"first {ns} of {n} points, K={k}, {len(times)} oracle steps from the same start "
+                      f"(median {ts:.3f} s/step)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    w = load_workload(args.workload, args.n)
+    orc = oracle.default()
+    x = w["x"]
+    n, k = x.shape[1], w["k"]
+    ns = min(n, 1 << 17)
+    xs = np.ascontiguousarray(x[:, :ns])
+    t0 = time.perf_counter()
+    orc.step(xs, w["mu0"])
+    t1 = time.perf_counter() - t0
+    budget = 120.0 / max(1, args.steps + args.warmup)  # whole run within ~2 minutes
+    ns = int(min(n, max(1024, ns * budget / max(t1, 1e-4))))
+    xs = np.ascontiguousarray(x[:, :ns])
+    mu = w["mu0"]
+    for _ in range(args.warmup):
+        orc.step(xs, mu)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, mu, _, _ = orc.step(xs, mu)
+    dt = time.perf_counter() - t0
+    val = ns * k * args.steps / dt
+    cores = orc.threads()
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": args.workload, "n": n, "d": x.shape[0], "k": k,
+                      "sample_points_per_step": ns},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"first {ns} of {n} points per step, successive Lloyd steps"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    import paper_2405_12052_gb300 as km
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    km.build()
+    w = load_workload(args.workload, args.n)
+    x, mu0, k = w["x"], w["mu0"], w["k"]
+    d, n = x.shape
+    xt = torch.from_numpy(x).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    g = km.KMeans(n, d, k, stream=stream)
+    g.set_points(xt, borrow=True)
+    g.set_init(mu0)
+    K, W = args.steps, args.warmup
+    g.begin(W + K, -1.0)  # tol < 0: never met, so exactly W + K steps run
+    for _ in range(W):
+        g.assign_async()
+        g.update_async()
+    torch.cuda.synchronize(dev)
+    ea = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    eb = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.2)
+    start.record(stream)
+    for i in range(K):
+        ea[i].record(stream)
+        g.assign_async()
+        eb[i].record(stream)
+        g.update_async()
+    end.record(stream)
+    end.synchronize()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(end)
+    st = g.sync()
+    assert st["iters"] == W + K, st
+    assign_ms = statistics.mean(ea[i].elapsed_time(eb[i]) for i in range(K))
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / K
+    value = n * k * K * ws / (total_ms / 1e3)
+    stats = g.stats()
+
+    # end to end through the public API with host buffers (pinned)
+    xp = torch.from_numpy(x).pin_memory()
+    lab_out = torch.empty(n, dtype=torch.int32).pin_memory()
+    e2e_times = []
+    g2 = km.KMeans(n, d, k, stream=stream)
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g2.set_points(xp)
+        g2.set_init(mu0)
+        g2.step()
+        g2.labels_host_into(lab_out)
+        dt = time.perf_counter() - t0
+        if i:
+            e2e_times.append(dt)
+    g2.close()
+    e2e_s = statistics.median(e2e_times)
+    e2e = {"value": n * k / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * d * 4 + k * d * 8,
+           "d2h_bytes_per_step": n * 4 + 16}
+
+    pk, src = peaks()
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak_tflops = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    flops = 3.0 * n * k * d
+    achieved = flops / (assign_ms / 1e3) / 1e12
+    traffic = profiled_traffic(args.workload, n, k, d)
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak_tflops, "traffic": traffic,
+            "kernel": "assign_fast_kernel<3>", "kernel_ms": assign_ms,
+            "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {mhz:.0f} MHz "
+                           f"(sm_max_mhz of {src} peaks); algorithmic 3*N*K*d flops per launch",
+            "hbm_frac_of_measured": (n * d * 4 / (assign_ms / 1e3) / 1e9) / float(pk.get("hbm_gbs", 6800.0))}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+           "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "n": n, "d": d, "k": k,
+                      "init": "k-means++ on a 2^20-point subsample",
+                      "l2": "points 1.2 GB > 129 MB L2: no flush needed" if n * d * 4 > 129e6 else "L2-resident",
+                      "parallelism": "single" if ws == 1 else f"replicas{ws}"},
+           "clocks": clk, "e2e": e2e, "gpu_launches": 2 * K, "roofline": roof,
+           "assign_ms": assign_ms, "update_ms": ms_step - assign_ms,
+           "flagged_per_step": stats["flagged"], "fp64_decided_per_step": stats["fp64_decided"]}
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    g.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,170 @@
+/*
+ * km.h -- C ABI of the GB300 (sm_103a) Lloyd's K-means library (libkm.so).
+ *
+ * The library runs the data-parallel hot path of Lloyd's algorithm as stated
+ * in "Parallelization of the K-Means Algorithm with Applications to Big Data
+ * Clustering" (arXiv 2405.12052):
+ *   - reassignment  z_i = argmin_k ||x_i - mu_k||_2^2
+ *                   (section "The Lloyd's algorithm", step 2);
+ *   - mean update   mu_k = sum_i 1(z_i = k) x_i / sum_i 1(z_i = k)
+ *                   (same section, step 3);
+ *   - error         E^2 = sum_k ||mu_k^{t+1} - mu_k^t||_2^2, loop until the
+ *                   error is below a tolerance (section "Serial Lloyd's
+ *                   algorithm").
+ * The inputs the paper names for its serial program are the dataset, the
+ * number of clusters and the number of points (same section); the outputs
+ * are the final cluster indicators and means.
+ *
+ * Conventions shared by every entry point
+ *   - Points are float32 in the paper's layout X in R^{d x N}: coordinate j of
+ *     point i is at x[j * ld + i] (KM_SOA_DxN), or row-major N x d
+ *     (KM_AOS_NxD, copied into the SoA layout on entry).
+ *   - Centroids are double, K x d, row-major.  Labels are int32 in 0..K-1
+ *     (the paper numbers clusters 1..K).
+ *   - Labels are exact: every point's label equals the argmin of the
+ *     double-precision squared distances sum_j (x_ij - mu_kj)^2 accumulated
+ *     over j in order, ties to the lowest k.  Points whose two nearest FP32
+ *     distances are within a rigorous error bound, or within 1e-5 relative,
+ *     are re-decided in double precision on the GPU.
+ *   - Per-cluster sums are exact integer (fixed-point) sums; centroids are
+ *     one rounding of sum / count.  An empty cluster keeps its centre.
+ *   - Every call returns a km_status.  A status < 0 leaves the context
+ *     usable only for km_last_error and km_destroy.  km_last_error returns a
+ *     message owned by the context, valid until the next call on it.
+ *   - Calls on one context are not thread-safe; distinct contexts are
+ *     independent.  Work is queued on the stream given in km_options (NULL:
+ *     a blocking stream the context creates, which orders itself after work
+ *     on the legacy default stream); calls that return host data synchronize
+ *     it.
+ *   - There is no CPU fallback: if no sm_103a device is present, km_create
+ *     returns KM_ECUDA.
+ */
+#ifndef KM_H
+#define KM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct km_ctx km_ctx; /* opaque; owns every device buffer it allocates */
+
+typedef enum {
+  KM_OK = 0,
+  KM_NOT_CONVERGED = 1, /* km_run reached max_iter; outputs are still valid */
+  KM_EINVAL = -1,       /* bad argument (null pointer, size, layout, K > N) */
+  KM_ENOMEM = -2,       /* device or host allocation failed */
+  KM_ECUDA = -3,        /* a CUDA call failed, or no usable device */
+  KM_ESTATE = -4,       /* step/run before km_set_points and km_set_init */
+  KM_ETIMEOUT = -5,     /* reserved: a bounded device wait gave up */
+  KM_ENUMERIC = -6      /* NaN/Inf in the points or centroids, or data out of range */
+} km_status;
+
+enum { KM_SOA_DxN = 0, KM_AOS_NxD = 1 };                       /* point layouts */
+enum { KM_HOST = 0, KM_DEVICE_COPY = 1, KM_DEVICE_BORROW = 2 }; /* where a buffer lives */
+enum { KM_E_NORM = 0, KM_E_SQUARED = 1 };                      /* which error km_run tests */
+
+typedef struct km_options {
+  int32_t e_mode;  /* KM_E_NORM (default): stop when sqrt(E^2) < tol;
+                      KM_E_SQUARED: the paper's E^2 = sum ||dmu||^2 < tol */
+  int32_t use_graph; /* 1 (default): km_run drives the loop from one CUDA graph
+                        with a device-side stop; 0: one host round trip per step */
+  double tie_rel;  /* relative near-tie threshold re-decided in FP64 (default 1e-5) */
+  void* stream;    /* cudaStream_t for all work (NULL: the context creates one) */
+} km_options;
+
+/* Fill *opt with the defaults above. */
+void km_default_options(km_options* opt);
+
+/* Create a context for N points of dimension d and K clusters on the current
+ * CUDA device.  opt may be NULL (defaults).  Allocates the per-context device
+ * buffers (labels, centroids, per-block partial sums).
+ * Errors: KM_EINVAL (out == NULL, n < 1, d < 1, k < 1, k > n),
+ *         KM_ECUDA (no sm_103a device), KM_ENOMEM. */
+km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_options* opt);
+
+/* Give the context its points X (section "The Lloyd's algorithm": X in
+ * R^{d x N}).  layout: KM_SOA_DxN (ld = elements between coordinate rows,
+ * >= N) or KM_AOS_NxD (ld = elements between points, >= d).  mem: KM_HOST
+ * (host pointer; copied to the device), KM_DEVICE_COPY (device pointer;
+ * copied), KM_DEVICE_BORROW (device SoA pointer kept as is: it must stay
+ * valid and unchanged until km_destroy or the next km_set_points; a pointer
+ * that is not 16-byte aligned, or an ld that is not a multiple of 4, is
+ * copied instead).  Scans the points once for their range; any NaN/Inf gives
+ * KM_ENUMERIC.  Synchronizes the stream. */
+km_status km_set_points(km_ctx* ctx, const float* x, int64_t ld, int32_t layout, int32_t mem);
+
+/* Set the starting centroids mu^0 (section "The Lloyd's algorithm", step 1),
+ * K x d row-major doubles in host memory, and reset the iteration count.
+ * Resuming from km_get_centroids output continues a run bit-identically.
+ * Errors: KM_EINVAL (null), KM_ENUMERIC (non-finite). */
+km_status km_set_init(km_ctx* ctx, const double* mu0);
+
+/* One Lloyd step from the current centroids: reassignment, mean update and
+ * error.  Writes E (sqrt of E^2) and E^2 to the non-NULL outputs and
+ * synchronizes the stream.  Errors: KM_ESTATE, KM_ECUDA. */
+km_status km_step(km_ctx* ctx, double* e_out, double* e2_out);
+
+/* Run steps until the selected error (km_options.e_mode) is < tol or max_iter
+ * steps have run (section "Serial Lloyd's algorithm").  Outputs (each may be
+ * NULL): labels_out (N int32, host memory) from the last step, centroids_out
+ * (K x d doubles, host), iters_out (steps run, including the one that met the
+ * tolerance), e_out (E of the last step).  Returns KM_OK when converged,
+ * KM_NOT_CONVERGED when max_iter was reached.  The iteration count restarts
+ * at km_set_init; a second km_run continues from the current centroids. */
+km_status km_run(km_ctx* ctx, int32_t max_iter, double tol, int32_t* labels_out,
+                 double* centroids_out, int32_t* iters_out, double* e_out);
+
+/* Asynchronous pieces of a step, for callers that drive (or capture into a
+ * CUDA graph) their own loop on the context's stream.  None of them
+ * synchronizes.  km_begin sets the stop rule for the steps that follow
+ * (max_iter counted from the current iteration, tol as in km_run); then each
+ * step is km_assign_async (reassignment and per-block sums, one kernel)
+ * followed by km_update_async (fixed-order reduction, divide, error and next
+ * screen tables, one kernel).  Once the stop rule has fired, further kernels
+ * return immediately.  km_sync reads the step count and error back.
+ * Errors: KM_ESTATE before points and centroids are set, KM_ECUDA. */
+km_status km_begin(km_ctx* ctx, int32_t max_iter, double tol);
+km_status km_assign_async(km_ctx* ctx);
+km_status km_update_async(km_ctx* ctx);
+km_status km_sync(km_ctx* ctx, int32_t* iters_out, double* e_out, int32_t* done_out);
+
+/* The stream the context queues its work on (a cudaStream_t). */
+void* km_stream(km_ctx* ctx);
+
+/* Copy results of the last step.  mem: KM_HOST or KM_DEVICE_COPY (device
+ * pointer of the caller).  Sizes: labels N int32, centroids K x d doubles,
+ * counts K int64.  Synchronize the stream. */
+km_status km_get_labels(km_ctx* ctx, int32_t* labels_out, int32_t mem);
+km_status km_get_centroids(km_ctx* ctx, double* centroids_out, int32_t mem);
+km_status km_get_counts(km_ctx* ctx, int64_t* counts_out);
+
+/* Diagnostics of the last step. */
+typedef struct km_stats {
+  int32_t iters;          /* steps since km_set_init */
+  int32_t converged;      /* 1 once the tolerance was met in km_run */
+  double e, e2;           /* error of the last step */
+  int64_t flagged;        /* points re-checked past the FP32 screen in the last step */
+  int64_t fp64_decided;   /* of those, points decided in FP64 */
+  int32_t empty_clusters; /* clusters with no points in the last step */
+  int32_t path;           /* 1: fused FFMA2 kernel (d <= 4, K <= 256); 2: generic kernel */
+} km_stats;
+km_status km_get_stats(km_ctx* ctx, km_stats* out);
+
+/* Device pointers owned by the context, for callers that keep data on the
+ * GPU (valid until km_destroy).  Points are the SoA copy (or the borrowed
+ * pointer) with row stride *ld_out. */
+km_status km_device_buffers(km_ctx* ctx, const float** points, int64_t* ld_out,
+                            int32_t** labels, double** centroids);
+
+const char* km_last_error(const km_ctx* ctx);
+void km_destroy(km_ctx* ctx);
+
+/* Library version string and the sm architecture it was built for. */
+const char* km_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KM_H */

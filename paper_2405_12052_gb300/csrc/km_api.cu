@@ -1,0 +1,505 @@
+// C ABI of libkm.so (declared in include/km.h): context, device buffers,
+// launches of the assign and update kernels, and the loop drivers (one host
+// round trip per step, or a CUDA graph of unrolled steps whose kernels stop
+// themselves once the device-side stop flag is set).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/km.h"
+#include "km_internal.cuh"
+
+using namespace km;
+
+struct km_ctx {
+  int64_t n = 0;
+  int d = 0, k = 0;
+  km_options opt{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int dev = 0, sms = 0;
+  bool fast = false;
+  int kpad = 0;
+  // points
+  float* x_own = nullptr;
+  const float* x = nullptr;
+  int64_t ld = 0;
+  bool have_points = false, have_init = false;
+  // per-step buffers
+  int32_t* labels = nullptr;
+  double* mu = nullptr;
+  long long* counts = nullptr;
+  long long* partials = nullptr;
+  int G = 0;
+  long long* s128 = nullptr;
+  int RB = 0;
+  unsigned long long* tab2 = nullptr;
+  float4* ctil4 = nullptr;
+  float* ctil = nullptr;
+  float* cnorm = nullptr;
+  float* shift = nullptr;
+  float* gen_bmax = nullptr;
+  DataConst* dc = nullptr;
+  IterConst* ic = nullptr;
+  LoopState* ls = nullptr;
+  float* scan = nullptr;  // [2d] min/max + [1] amax
+  unsigned long long* scan_bad = nullptr;
+  size_t fast_smem = 0;
+  float A_max = 0.f;
+  int G0 = 0;
+  // loop
+  cudaGraphExec_t graph = nullptr;
+  int graph_unroll = 16;
+  LoopState host_ls{};
+  std::string err;
+};
+
+namespace {
+
+km_status fail(km_ctx* c, km_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define KM_CUDA(ctx, call)                                                                   \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? KM_ENOMEM : KM_ECUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
+}
+
+void free_all(km_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  void* bufs[] = {c->x_own, c->labels, c->mu, c->counts, c->partials, c->s128, c->tab2,
+                  c->ctil4, c->ctil, c->cnorm, c->shift, c->gen_bmax, c->dc, c->ic, c->ls,
+                  c->scan, c->scan_bad};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+}
+
+UpdateArgs update_args(km_ctx* c) {
+  UpdateArgs u{};
+  u.partials = c->partials; u.G = c->G; u.k = c->k; u.d = c->d;
+  u.s128 = c->s128; u.RB = c->RB;
+  u.mu = c->mu; u.counts = c->counts;
+  u.dc = c->dc; u.ic = c->ic; u.ls = c->ls;
+  u.tab2 = c->tab2; u.ctil4 = c->ctil4; u.ctil = c->ctil; u.cnorm = c->cnorm;
+  u.shift = c->shift; u.kpad = c->kpad; u.fast = c->fast ? 1 : 0;
+  u.tie_rel = c->opt.tie_rel; u.A_max = c->A_max; u.gen_bmax = c->gen_bmax;
+  return u;
+}
+
+// Reassignment + per-block sums (one kernel).
+cudaError_t launch_assign(km_ctx* c) {
+  cudaError_t e;
+  if (c->fast) {
+    FastArgs a{};
+    a.x = c->x; a.ld = c->ld; a.n = c->n; a.k = c->k; a.kpad = c->kpad;
+    a.tab2 = c->tab2; a.ctil = c->ctil4; a.mu = c->mu; a.ic = c->ic; a.dc = c->dc;
+    a.ls = c->ls; a.labels = c->labels; a.partials = c->partials;
+    a.ntiles = (c->n + kTile - 1) / kTile;
+    e = launch_assign_fast(c->d, c->G, c->fast_smem, c->st, a);
+  } else {
+    GenericArgs a{};
+    a.x = c->x; a.ld = c->ld; a.n = c->n; a.d = c->d; a.k = c->k;
+    a.ctil = c->ctil; a.cnorm = c->cnorm; a.mu = c->mu; a.shift = c->shift; a.dc = c->dc;
+    a.ls = c->ls; a.labels = c->labels; a.partials = c->partials;
+    a.A_max = c->A_max; a.B_max_ptr = c->gen_bmax; a.tau = (float)(c->opt.tie_rel * (1.0 + 1e-4));
+    e = launch_assign_generic(c->G, 0, c->st, a);
+  }
+  return e;
+}
+
+// One step: assign + accumulate, then reduce + divide + error + next tables.
+cudaError_t launch_step(km_ctx* c) {
+  cudaError_t e = launch_assign(c);
+  if (e != cudaSuccess) return e;
+  return launch_update(c->st, update_args(c));
+}
+
+km_status write_control(km_ctx* c, int done, int max_iter_abs, double tol) {
+  LoopControl lc{};
+  lc.done = done;
+  lc.max_iter = max_iter_abs;
+  lc.e_mode = c->opt.e_mode;
+  lc.converged = 0;
+  lc.tol = tol;
+  KM_CUDA(c, cudaMemcpyAsync(c->ls, &lc, sizeof(lc), cudaMemcpyHostToDevice, c->st));
+  return KM_OK;
+}
+
+km_status read_state(km_ctx* c) {
+  KM_CUDA(c, cudaMemcpyAsync(&c->host_ls, c->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, c->st));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  if (c->host_ls.error)
+    return fail(c, KM_ECUDA, "device error word set (" + std::to_string(c->host_ls.error) + ")");
+  return KM_OK;
+}
+
+km_status ready(km_ctx* c) {
+  if (!c) return KM_EINVAL;
+  if (!c->have_points || !c->have_init)
+    return fail(c, KM_ESTATE, "km_set_points and km_set_init must come first");
+  return KM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void km_default_options(km_options* opt) {
+  if (!opt) return;
+  opt->e_mode = KM_E_NORM;
+  opt->use_graph = 1;
+  opt->tie_rel = 1e-5;
+  opt->stream = nullptr;
+}
+
+const char* km_version(void) { return "libkm 0.1 (sm_103a)"; }
+
+km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_options* opt) {
+  if (!out) return KM_EINVAL;
+  *out = nullptr;
+  if (n < 1 || d < 1 || k < 1 || k > n || n > (int64_t(1) << 40) || d > 4096 || k > (1 << 20))
+    return KM_EINVAL;
+  km_ctx* c = new (std::nothrow) km_ctx();
+  if (!c) return KM_ENOMEM;
+  *out = c;
+  c->n = n; c->d = d; c->k = k;
+  km_default_options(&c->opt);
+  if (opt) c->opt = *opt;
+  if (!(c->opt.tie_rel >= 0.0 && c->opt.tie_rel < 0.5)) return fail(c, KM_EINVAL, "tie_rel out of range");
+  if (c->opt.e_mode != KM_E_NORM && c->opt.e_mode != KM_E_SQUARED) return fail(c, KM_EINVAL, "bad e_mode");
+  KM_CUDA(c, cudaGetDevice(&c->dev));
+  cudaDeviceProp p{};
+  KM_CUDA(c, cudaGetDeviceProperties(&p, c->dev));
+  if (!(p.major == 10 && p.minor == 3))
+    return fail(c, KM_ECUDA, std::string("libkm is built for sm_103a; device is ") + p.name);
+  c->sms = p.multiProcessorCount;
+  if (c->opt.stream) {
+    c->st = static_cast<cudaStream_t>(c->opt.stream);
+  } else {
+    KM_CUDA(c, cudaStreamCreate(&c->st));  // blocking: ordered after legacy-stream work
+    c->own_stream = true;
+  }
+  c->kpad = k + (k & 1);
+  c->fast = d <= kMaxDFast && k <= kMaxKFast;
+  if (c->fast) {
+    c->fast_smem = fast_smem_bytes(d, c->kpad, k);
+    if (c->fast_smem > (size_t)p.sharedMemPerBlockOptin) c->fast = false;
+  }
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  if (c->fast) {
+    const int bpsm = fast_blocks_per_sm(d, c->fast_smem);
+    int64_t g = std::min<int64_t>(ntiles, (int64_t)c->sms * bpsm);
+    g = std::max<int64_t>(g, (ntiles * kTile + kMaxPointsPerBlock - 1) / kMaxPointsPerBlock);
+    c->G = (int)std::max<int64_t>(g, 1);
+  } else {
+    int64_t g = std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)c->sms * 8);
+    g = std::max<int64_t>(g, (n + kMaxPointsPerBlock - 1) / kMaxPointsPerBlock);
+    c->G = (int)std::max<int64_t>(g, 1);
+  }
+  c->RB = (int)std::max<int64_t>(1, std::min<int64_t>(16, (c->G + kWarps * 4 - 1) / (kWarps * 4)));
+  const size_t cols = (size_t)k * (d + 1);
+  KM_CUDA(c, dalloc(&c->labels, (size_t)n));
+  KM_CUDA(c, dalloc(&c->mu, (size_t)k * d));
+  KM_CUDA(c, dalloc(&c->counts, (size_t)k));
+  KM_CUDA(c, dalloc(&c->partials, (size_t)c->G * cols));
+  KM_CUDA(c, dalloc(&c->s128, (size_t)c->RB * cols * 2));
+  KM_CUDA(c, dalloc(&c->tab2, (size_t)c->kpad * (d + 1)));
+  KM_CUDA(c, dalloc(&c->ctil4, (size_t)k));
+  KM_CUDA(c, dalloc(&c->ctil, (size_t)k * d));
+  KM_CUDA(c, dalloc(&c->cnorm, (size_t)k));
+  KM_CUDA(c, dalloc(&c->shift, (size_t)d));
+  KM_CUDA(c, dalloc(&c->gen_bmax, 1));
+  KM_CUDA(c, dalloc(&c->dc, 1));
+  KM_CUDA(c, dalloc(&c->ic, 1));
+  KM_CUDA(c, dalloc(&c->ls, 1));
+  KM_CUDA(c, dalloc(&c->scan, (size_t)2 * d + 1));
+  KM_CUDA(c, dalloc(&c->scan_bad, 1));
+  KM_CUDA(c, cudaMemsetAsync(c->ls, 0, sizeof(LoopState), c->st));
+  KM_CUDA(c, cudaMemsetAsync(c->counts, 0, sizeof(long long) * k, c->st));
+  KM_CUDA(c, cudaMemsetAsync(c->labels, 0, sizeof(int32_t) * n, c->st));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  return KM_OK;
+}
+
+km_status km_set_points(km_ctx* c, const float* x, int64_t ld, int32_t layout, int32_t mem) {
+  if (!c) return KM_EINVAL;
+  if (!x) return fail(c, KM_EINVAL, "null points");
+  if (layout != KM_SOA_DxN && layout != KM_AOS_NxD) return fail(c, KM_EINVAL, "bad layout");
+  if (mem != KM_HOST && mem != KM_DEVICE_COPY && mem != KM_DEVICE_BORROW)
+    return fail(c, KM_EINVAL, "bad memory kind");
+  if (layout == KM_SOA_DxN && ld < c->n) return fail(c, KM_EINVAL, "ld < N for the d x N layout");
+  if (layout == KM_AOS_NxD && ld < c->d) return fail(c, KM_EINVAL, "ld < d for the N x d layout");
+  if (layout == KM_AOS_NxD && mem == KM_DEVICE_BORROW)
+    return fail(c, KM_EINVAL, "only the d x N layout can be borrowed");
+  c->have_points = false;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  const int d = c->d;
+  const int64_t n = c->n;
+  bool borrow = mem == KM_DEVICE_BORROW && (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (ld % 4 == 0);
+  if (borrow) {
+    c->x = x;
+    c->ld = ld;
+  } else {
+    const int64_t ldo = (n + 63) / 64 * 64;
+    if (!c->x_own) KM_CUDA(c, dalloc(&c->x_own, (size_t)d * ldo));
+    c->ld = ldo;
+    c->x = c->x_own;
+    if (layout == KM_SOA_DxN) {
+      KM_CUDA(c, cudaMemcpy2DAsync(c->x_own, ldo * 4, x, ld * 4, n * 4, d,
+                                   mem == KM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                   c->st));
+    } else {
+      const float* src = x;
+      float* tmp = nullptr;
+      if (mem == KM_HOST) {
+        KM_CUDA(c, dalloc(&tmp, (size_t)n * ld));
+        KM_CUDA(c, cudaMemcpyAsync(tmp, x, sizeof(float) * n * ld, cudaMemcpyHostToDevice, c->st));
+        src = tmp;
+      }
+      cudaError_t e = launch_aos_to_soa(src, ld, n, d, c->x_own, ldo, c->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+      if (tmp) cudaFree(tmp);
+      KM_CUDA(c, e);
+    }
+  }
+  // Range scan: shift, fixed-point grid, non-finite values.
+  float* mn = c->scan;
+  float* mx = c->scan + d;
+  KM_CUDA(c, launch_scan_range(c->x, c->ld, n, d, mn, mx, c->scan_bad, c->st));
+  std::vector<uint32_t> hmn(d), hmx(d);
+  unsigned long long bad = 0;
+  KM_CUDA(c, cudaMemcpyAsync(hmn.data(), mn, 4 * d, cudaMemcpyDeviceToHost, c->st));
+  KM_CUDA(c, cudaMemcpyAsync(hmx.data(), mx, 4 * d, cudaMemcpyDeviceToHost, c->st));
+  KM_CUDA(c, cudaMemcpyAsync(&bad, c->scan_bad, 8, cudaMemcpyDeviceToHost, c->st));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  if (bad) return fail(c, KM_ENUMERIC, std::to_string(bad) + " non-finite coordinate(s) in the points");
+  auto decode = [](uint32_t o) {
+    uint32_t b = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
+  };
+  std::vector<float> shift(d);
+  double absmax = 0.0;
+  for (int j = 0; j < d; ++j) {
+    const double lo = decode(hmn[j]), hi = decode(hmx[j]);
+    shift[j] = (float)(0.5 * (lo + hi));
+    absmax = std::max(absmax, std::max(std::fabs(lo), std::fabs(hi)));
+  }
+  int ex = absmax > 0.0 ? (int)std::floor(std::log2(absmax)) + 2 : -60;
+  if (absmax > 0.0 && std::ldexp(1.0, ex - 1) <= absmax) ++ex;  // guard log2 rounding
+  ex = std::max(ex, -60);
+  if (ex > 100) return fail(c, KM_ENUMERIC, "coordinates too large for the fixed-point sums (|x| >= 2^99)");
+  DataConst hdc{};
+  for (int j = 0; j < kMaxDFast; ++j) hdc.s[j] = j < d ? shift[j] : 0.f;
+  hdc.G0 = ex - 44;
+  hdc.C_hi = std::ldexp(1.5f, ex + 1);
+  hdc.C_lo = std::ldexp(1.5f, ex - 21);
+  std::memcpy(&hdc.bits_C_hi, &hdc.C_hi, 4);
+  std::memcpy(&hdc.bits_C_lo, &hdc.C_lo, 4);
+  KM_CUDA(c, cudaMemcpyAsync(c->shift, shift.data(), 4 * d, cudaMemcpyHostToDevice, c->st));
+  float* amax = c->scan + 2 * d;
+  KM_CUDA(c, launch_scan_amax(c->x, c->ld, n, d, c->shift, amax, c->st));
+  float ha = 0.f;
+  KM_CUDA(c, cudaMemcpyAsync(&ha, amax, 4, cudaMemcpyDeviceToHost, c->st));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  hdc.A_max = ha;
+  c->A_max = ha;
+  c->G0 = hdc.G0;
+  KM_CUDA(c, cudaMemcpyAsync(c->dc, &hdc, sizeof(hdc), cudaMemcpyHostToDevice, c->st));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  c->have_points = true;
+  if (c->have_init) {  // tables depend on the shift and A_max
+    KM_CUDA(c, launch_prepare(c->st, update_args(c)));
+    KM_CUDA(c, cudaStreamSynchronize(c->st));
+  }
+  return KM_OK;
+}
+
+km_status km_set_init(km_ctx* c, const double* mu0) {
+  if (!c) return KM_EINVAL;
+  if (!mu0) return fail(c, KM_EINVAL, "null centroids");
+  const size_t kd = (size_t)c->k * c->d;
+  for (size_t q = 0; q < kd; ++q)
+    if (!std::isfinite(mu0[q])) return fail(c, KM_ENUMERIC, "non-finite starting centroid");
+  KM_CUDA(c, cudaMemcpyAsync(c->mu, mu0, sizeof(double) * kd, cudaMemcpyHostToDevice, c->st));
+  KM_CUDA(c, cudaMemsetAsync(c->ls, 0, sizeof(LoopState), c->st));
+  c->have_init = true;
+  if (c->have_points) KM_CUDA(c, launch_prepare(c->st, update_args(c)));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  std::memset(&c->host_ls, 0, sizeof(c->host_ls));
+  return KM_OK;
+}
+
+km_status km_step(km_ctx* c, double* e_out, double* e2_out) {
+  km_status s = ready(c);
+  if (s != KM_OK) return s;
+  s = write_control(c, 0, 0x7fffffff, -1.0);
+  if (s != KM_OK) return s;
+  KM_CUDA(c, launch_step(c));
+  s = read_state(c);
+  if (s != KM_OK) return s;
+  if (e_out) *e_out = c->host_ls.E;
+  if (e2_out) *e2_out = c->host_ls.E2;
+  return KM_OK;
+}
+
+km_status km_run(km_ctx* c, int32_t max_iter, double tol, int32_t* labels_out,
+                 double* centroids_out, int32_t* iters_out, double* e_out) {
+  km_status s = ready(c);
+  if (s != KM_OK) return s;
+  if (max_iter < 0) return fail(c, KM_EINVAL, "max_iter < 0");
+  s = read_state(c);
+  if (s != KM_OK) return s;
+  const int start = c->host_ls.iter;
+  if (max_iter > 0) {
+    s = write_control(c, 0, start + max_iter, tol);
+    if (s != KM_OK) return s;
+    if (c->opt.use_graph) {
+      if (!c->graph) {
+        cudaGraph_t g = nullptr;
+        KM_CUDA(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int u = 0; u < c->graph_unroll && e == cudaSuccess; ++u) e = launch_step(c);
+        cudaError_t e2 = cudaStreamEndCapture(c->st, &g);
+        KM_CUDA(c, e);
+        KM_CUDA(c, e2);
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        KM_CUDA(c, e);
+      }
+      while (true) {
+        KM_CUDA(c, cudaGraphLaunch(c->graph, c->st));
+        s = read_state(c);
+        if (s != KM_OK) return s;
+        if (c->host_ls.done) break;
+      }
+    } else {
+      while (true) {
+        KM_CUDA(c, launch_step(c));
+        s = read_state(c);
+        if (s != KM_OK) return s;
+        if (c->host_ls.done) break;
+      }
+    }
+  }
+  if (labels_out)
+    KM_CUDA(c, cudaMemcpyAsync(labels_out, c->labels, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st));
+  if (centroids_out)
+    KM_CUDA(c, cudaMemcpyAsync(centroids_out, c->mu, sizeof(double) * c->k * c->d, cudaMemcpyDeviceToHost, c->st));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  if (iters_out) *iters_out = c->host_ls.iter - start;
+  if (e_out) *e_out = c->host_ls.E;
+  return c->host_ls.converged ? KM_OK : KM_NOT_CONVERGED;
+}
+
+km_status km_begin(km_ctx* c, int32_t max_iter, double tol) {
+  km_status s = ready(c);
+  if (s != KM_OK) return s;
+  if (max_iter < 0) return fail(c, KM_EINVAL, "max_iter < 0");
+  s = read_state(c);
+  if (s != KM_OK) return s;
+  return write_control(c, 0, c->host_ls.iter + max_iter, tol);
+}
+
+km_status km_assign_async(km_ctx* c) {
+  km_status s = ready(c);
+  if (s != KM_OK) return s;
+  KM_CUDA(c, launch_assign(c));
+  return KM_OK;
+}
+
+km_status km_update_async(km_ctx* c) {
+  km_status s = ready(c);
+  if (s != KM_OK) return s;
+  KM_CUDA(c, launch_update(c->st, update_args(c)));
+  return KM_OK;
+}
+
+km_status km_sync(km_ctx* c, int32_t* iters_out, double* e_out, int32_t* done_out) {
+  if (!c) return KM_EINVAL;
+  km_status s = read_state(c);
+  if (s != KM_OK) return s;
+  if (iters_out) *iters_out = c->host_ls.iter;
+  if (e_out) *e_out = c->host_ls.E;
+  if (done_out) *done_out = c->host_ls.done;
+  return KM_OK;
+}
+
+void* km_stream(km_ctx* c) { return c ? (void*)c->st : nullptr; }
+
+km_status km_get_labels(km_ctx* c, int32_t* out, int32_t mem) {
+  if (!c) return KM_EINVAL;
+  if (!out || (mem != KM_HOST && mem != KM_DEVICE_COPY)) return fail(c, KM_EINVAL, "bad output");
+  KM_CUDA(c, cudaMemcpyAsync(out, c->labels, sizeof(int32_t) * c->n,
+                             mem == KM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  return KM_OK;
+}
+
+km_status km_get_centroids(km_ctx* c, double* out, int32_t mem) {
+  if (!c) return KM_EINVAL;
+  if (!out || (mem != KM_HOST && mem != KM_DEVICE_COPY)) return fail(c, KM_EINVAL, "bad output");
+  KM_CUDA(c, cudaMemcpyAsync(out, c->mu, sizeof(double) * c->k * c->d,
+                             mem == KM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  return KM_OK;
+}
+
+km_status km_get_counts(km_ctx* c, int64_t* out) {
+  if (!c) return KM_EINVAL;
+  if (!out) return fail(c, KM_EINVAL, "null output");
+  KM_CUDA(c, cudaMemcpyAsync(out, c->counts, sizeof(int64_t) * c->k, cudaMemcpyDeviceToHost, c->st));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  return KM_OK;
+}
+
+km_status km_get_stats(km_ctx* c, km_stats* out) {
+  if (!c) return KM_EINVAL;
+  if (!out) return fail(c, KM_EINVAL, "null output");
+  km_status s = read_state(c);
+  if (s != KM_OK) return s;
+  out->iters = c->host_ls.iter;
+  out->converged = c->host_ls.converged;
+  out->e = c->host_ls.E;
+  out->e2 = c->host_ls.E2;
+  out->flagged = (int64_t)c->host_ls.last_flagged;
+  out->fp64_decided = (int64_t)c->host_ls.last_fp64;
+  out->empty_clusters = c->host_ls.empty;
+  out->path = c->fast ? 1 : 2;
+  return KM_OK;
+}
+
+km_status km_device_buffers(km_ctx* c, const float** points, int64_t* ld_out, int32_t** labels,
+                            double** centroids) {
+  if (!c) return KM_EINVAL;
+  if (points) *points = c->x;
+  if (ld_out) *ld_out = c->ld;
+  if (labels) *labels = c->labels;
+  if (centroids) *centroids = c->mu;
+  return KM_OK;
+}
+
+const char* km_last_error(const km_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void km_destroy(km_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  free_all(c);
+  delete c;
+}
+
+}  // extern "C"

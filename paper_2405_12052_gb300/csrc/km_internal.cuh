@@ -1,0 +1,158 @@
+// Internal definitions shared by the kernels and the C ABI of libkm.so.
+//
+// Numerical scheme of one Lloyd step (reassignment, mean update, error; the
+// paper's section "The Lloyd's algorithm" and section "Serial Lloyd's
+// algorithm"):
+//
+// Screen (FP32).  With a per-dataset shift s, x~ = fl(x - s) and
+// c~_k = fl32(mu_k - s), the kernel ranks W_k = ||c~_k||^2 - 2 x~.c~_k, which
+// differs from D_ik = ||x_i - mu_k||^2 by a per-point constant.  The value is
+// evaluated as r = M + 2^sigma W_k by an FMA chain whose every intermediate
+// lies in one binade [2^eM, 2^(eM+1)) (M and sigma are chosen each step from
+// bounds on ||x~||^2 and ||c~||^2), so every rounding is at most half an ulp
+// of that binade.  The bits of r shifted left by L, plus k, form a positive
+// float whose order is (r, k): top-2 tracking then needs only FMNMX.
+//
+// Flag.  A point is re-checked unless the gap between its two smallest r
+// exceeds a rigorous bound on every error (input roundings, chain roundings,
+// the oracle's own FP64 roundings) plus tie_rel * D2.  Flagged points go to a
+// per-block queue and are decided by an FP32 direct-form pass with its own
+// bound, and if that is not conclusive (or the two nearest are within
+// tie_rel), by FP64 in the exact expression order sum_j (x_j - mu_kj)^2.
+//
+// Sums.  Each coordinate is split exactly into two integers on fixed grids
+// (x = hi 2^G1 + lo 2^G0 up to a quantisation below 2^(G0-1), G1 = G0 + 22)
+// with FP32 magic-number additions; the biased bit patterns are added with
+// 32-bit shared-memory atomics (integer, so order-independent) into per-warp
+// windows that are flushed into int64 per-warp totals.  Per-block int64
+// partials are reduced in a fixed order in int128 and converted once.
+#pragma once
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace km {
+
+constexpr int kMaxDFast = 4;        // fused FFMA2 kernel: d <= 4
+constexpr int kMaxKFast = 256;      // and K <= 256 (index in <= 8 low bits)
+constexpr int kThreads = 256;       // threads per block of the assign kernels
+constexpr int kWarps = kThreads / 32;
+constexpr int kPts = 8;             // points per thread per tile (fused kernel)
+constexpr int kTile = kThreads * kPts;  // 2048 points per block per tile
+constexpr int kQueueCap = 6144;     // flagged points queued per block (drained above 4096)
+constexpr int64_t kMaxPointsPerBlock = int64_t(1) << 19;
+
+// Per-dataset constants, fixed by km_set_points.
+struct DataConst {
+  float s[kMaxDFast];   // shift used by the screen (fused kernel)
+  float A_max;          // max_i fl32 ||fl(x_i - s)||^2 with the kernel's expression
+  int G0;               // fixed-point grid exponent of the low limb
+  float C_hi, C_lo;     // 1.5 * 2^(G0+45), 1.5 * 2^(G0+23)
+  uint32_t bits_C_hi, bits_C_lo;
+};
+
+// Per-step constants of the screen, written by the update kernel.
+struct IterConst {
+  float M;              // bias, 2^eM * (1.5 | 1.25 | 1.375)
+  uint32_t bitsM_low;   // bits(M) with the top L bits cleared
+  uint32_t mul;         // 2^L
+  int L;                // index bits
+  float thr_c0;         // flag threshold, constant part (ulps of the binade)
+  float thr_cA;         // per unit of ||x~||^2 (ulps)
+  float tau;            // tie_rel * (1 + 1e-4)
+  float G;              // 2^(sigma - eM + 23): unscaled -> ulps
+  float B_max;          // max_k ||c~_k||^2 (FP32, rounded up)
+  float pad[3];
+};
+
+// Loop state on the device.  The first 24 bytes are control fields written
+// by the host before a run or a step; the rest is written by the kernels.
+struct LoopState {
+  int32_t done;         // 1: the stop test passed or max_iter reached
+  int32_t max_iter;     // absolute iteration count at which to stop
+  int32_t e_mode;       // 0: test sqrt(E^2); 1: test E^2
+  int32_t converged;    // set by the update kernel when the test passes
+  double tol;
+  int32_t iter;         // steps done since set_init
+  int32_t empty;        // empty clusters in the last step
+  double E, E2;         // error of the last step
+  unsigned long long flagged;       // accumulating during a step
+  unsigned long long fp64_decided;  // accumulating during a step
+  unsigned long long last_flagged;  // of the last completed step
+  unsigned long long last_fp64;
+  unsigned int ticket;              // last-block counter of the reduction
+  int32_t error;                    // sticky device error word (0 = none)
+};
+struct LoopControl {
+  int32_t done, max_iter, e_mode, converged;
+  double tol;
+};
+static_assert(sizeof(LoopControl) == 24, "control block layout");
+
+struct FastArgs {
+  const float* x; int64_t ld; int64_t n; int k; int kpad;
+  const unsigned long long* tab2;  // [kpad][D+1] packed (a, a) float pairs
+  const float4* ctil;              // [k] (c~_0.., B_k) fp32 table for the re-check
+  const double* mu;                // [k][D] current centroids (FP64)
+  const IterConst* ic;
+  const DataConst* dc;
+  LoopState* ls;
+  int32_t* labels;
+  long long* partials;             // [gridDim.x][k][D+1]
+  int64_t ntiles;
+};
+
+struct GenericArgs {
+  const float* x; int64_t ld; int64_t n; int d; int k;
+  const float* ctil;               // [k][d] fp32 (mu - s)
+  const float* cnorm;              // [k] ||c~||^2 fp32 (unused by the direct form)
+  const double* mu;                // [k][d]
+  const float* shift;              // [d]
+  const DataConst* dc;
+  LoopState* ls;
+  int32_t* labels;
+  long long* partials;             // [gridDim.x][k][d+1]
+  float A_max;
+  const float* B_max_ptr;          // max_k ||c~_k||^2, written by the update kernel
+  float tau;
+};
+
+// Host-side launchers (defined in the .cu files).
+cudaError_t launch_assign_fast(int d, int grid, size_t smem, cudaStream_t st, const FastArgs& a);
+size_t fast_smem_bytes(int d, int kpad, int k);
+int fast_blocks_per_sm(int d, size_t smem);
+cudaError_t launch_assign_generic(int grid, size_t smem, cudaStream_t st, const GenericArgs& a);
+size_t generic_smem_bytes(int d, int k);
+
+struct UpdateArgs {
+  const long long* partials; int G; int k; int d;
+  long long* s128;                 // [RB][k][d+1][2] per-row-block int128 partial sums
+  int RB;
+  double* mu;                      // [k][d] in/out
+  long long* counts;               // [k]
+  const DataConst* dc;
+  IterConst* ic;
+  LoopState* ls;
+  unsigned long long* tab2;        // out: next step's screen table [kpad][d+1]
+  float4* ctil4;                   // out (d <= 4)
+  float* ctil;                     // out (generic) [k][d]
+  float* cnorm;                    // out (generic) [k]
+  const float* shift;              // [d] generic shift
+  int kpad;
+  int fast;                        // 1: fused kernel tables
+  double tie_rel;
+  float A_max;
+  float* gen_bmax;                 // out (generic)
+};
+cudaError_t launch_update(cudaStream_t st, const UpdateArgs& a);
+cudaError_t launch_prepare(cudaStream_t st, const UpdateArgs& a);  // tables from mu, no step
+
+// Data scan: per-coordinate min/max, absmax, non-finite count.
+cudaError_t launch_scan_range(const float* x, int64_t ld, int64_t n, int d, float* mn, float* mx,
+                              unsigned long long* nonfinite, cudaStream_t st);
+cudaError_t launch_scan_amax(const float* x, int64_t ld, int64_t n, int d, const float* shift,
+                             float* amax, cudaStream_t st);
+cudaError_t launch_aos_to_soa(const float* src, int64_t lds, int64_t n, int d, float* dst,
+                              int64_t ldd, cudaStream_t st);
+
+}  // namespace km

@@ -1,0 +1,377 @@
+// Mean calculation and convergence error of Lloyd's algorithm (paper,
+// section "The Lloyd's algorithm", step 3, and section "Serial Lloyd's
+// algorithm"), plus the per-dataset scans that size the FP32 screen and the
+// fixed-point grid.
+//
+// reduce_update_kernel: every block sums its slice of the per-block int64
+// partials in int128 (rows in a fixed order), the last block to finish
+// (integer ticket) adds the row-block sums in a fixed order, divides
+// mu_k = S_k / n_k (an empty cluster keeps mu_k), forms E^2 with a fixed-order
+// tree, tests the stop rule, and writes the next step's screen tables.
+#include "km_internal.cuh"
+
+namespace km {
+
+namespace {
+
+__device__ __forceinline__ double i128_to_double(long long lo_s, long long hi_s) {
+  // value = hi * 2^64 + (unsigned)lo, two's complement; correctly rounded.
+  unsigned long long lo = (unsigned long long)lo_s, hi = (unsigned long long)hi_s;
+  bool neg = (long long)hi < 0;
+  if (neg) {  // negate the 128-bit value
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  double r;
+  if (hi == 0ull) {
+    r = __ull2double_rn(lo);
+  } else {
+    int sh = 64 - __clzll((long long)hi);  // bits used in hi
+    unsigned long long top = (hi << (64 - sh)) | (lo >> sh);
+    unsigned long long rest = lo << (64 - sh);
+    if (rest) top |= 1ull;  // sticky bit, 11 places below the rounding point
+    r = ldexp(__ull2double_rn(top), sh);
+  }
+  return neg ? -r : r;
+}
+
+__device__ __forceinline__ void add128(unsigned long long& lo, long long& hi, long long v) {
+  unsigned long long nl = lo + (unsigned long long)v;
+  hi += (v < 0 ? -1ll : 0ll) + (nl < lo ? 1ll : 0ll);
+  lo = nl;
+}
+__device__ __forceinline__ void add128p(unsigned long long& lo, long long& hi, unsigned long long vl,
+                                        long long vh) {
+  unsigned long long nl = lo + vl;
+  hi += vh + (nl < lo ? 1ll : 0ll);
+  lo = nl;
+}
+
+__device__ __forceinline__ uint32_t ordered(float f) {
+  uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Screen tables for the next step from mu (one block).  Fused path: c~ and
+// ||c~||^2, the bias M, the scale sigma and the flag constants; generic
+// path: c~ and B_max only.
+__device__ void prepare_tables(const UpdateArgs& a, double* sB) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nth = blockDim.x * blockDim.y;
+  const int k = a.k, d = a.d;
+  __shared__ double sh_bmax;
+  __shared__ int sh_sigma;
+  __shared__ double sh_M, sh_dummy;
+  if (a.fast) {
+    const DataConst* dc = a.dc;
+    for (int c = tid; c < k; c += nth) {
+      float cv[4] = {0.f, 0.f, 0.f, 0.f};
+      double B = 0.0;
+      for (int j = 0; j < d; ++j) {
+        cv[j] = __double2float_rn(__dsub_rn(a.mu[(size_t)c * d + j], (double)dc->s[j]));
+        B = __dadd_rn(B, __dmul_rn((double)cv[j], (double)cv[j]));
+      }
+      a.ctil4[c] = make_float4(cv[0], cv[1], cv[2], cv[3]);
+      sB[c] = B;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double bmax = 0.0;
+      for (int c = 0; c < k; ++c) bmax = fmax(bmax, sB[c]);
+      const int kpad = a.kpad;
+      int L = 1;
+      while ((1 << L) < kpad) ++L;
+      int E;
+      double frac, hw;
+      if (L <= 6) {
+        const int base = 1 << (7 - L), step = 1 << (9 - L);
+        E = base + ((127 - base) / step) * step;
+        frac = 1.5; hw = 0.5;
+      } else if (L == 7) {
+        E = 125; frac = 1.25; hw = 0.25;
+      } else {
+        E = 126; frac = 1.375; hw = 0.125;
+      }
+      const int eM = E - 127;
+      const double M = ldexp(frac, eM);
+      const double top = ldexp(hw, eM);
+      const double P = (dc->A_max * (1.0 + 0x1p-20) + 2.0 * bmax) * (1.0 + 0x1p-10) + 1e-300;
+      int sigma = ilogb(top / P);
+      if (ldexp(P, sigma) >= top) sigma -= 1;
+      sigma = max(-120, min(120, sigma));
+      const double G = ldexp(1.0, sigma - eM + 23);
+      const double u = 0x1p-24, u64x = 4.1 * 0x1p-53;
+      IterConst ic;
+      ic.M = (float)M;
+      ic.L = L;
+      ic.mul = 1u << L;
+      ic.bitsM_low = __float_as_uint(ic.M) & ((1u << (32 - L)) - 1u);
+      ic.G = (float)G;
+      ic.thr_c0 = __double2float_ru(((double)(d + 1) + 2.0 + (8.002 * u + u64x * (d + 1)) * bmax * G) *
+                                    (1.0 + 1e-4));
+      ic.thr_cA = __double2float_ru((4.001 * u + u64x * (d + 1)) * G * (1.0 + 1e-4) * (1.0 + 1e-5));
+      ic.tau = __double2float_ru(a.tie_rel * (1.0 + 1e-4));
+      ic.B_max = __double2float_ru(bmax);
+      ic.pad[0] = ic.pad[1] = ic.pad[2] = 0.f;
+      *a.ic = ic;
+      sh_bmax = bmax;
+      sh_sigma = sigma;
+      sh_M = M;
+      sh_dummy = (L <= 6 ? ldexp(2.0 - 0x1p-23, eM) : ldexp(1.5 - 0x1p-23, eM));
+    }
+    __syncthreads();
+    const int sigma = sh_sigma, dp = d + 1;
+    const float scale = -ldexpf(1.0f, sigma + 1);
+    for (int c = tid; c < a.kpad; c += nth) {
+      unsigned long long* row = a.tab2 + (size_t)c * dp;
+      if (c < k) {
+        const float4 cv4 = a.ctil4[c];
+        const float cv[4] = {cv4.x, cv4.y, cv4.z, cv4.w};
+        for (int j = 0; j < d; ++j) {
+          const uint32_t b = __float_as_uint(__fmul_rn(cv[j], scale));
+          row[j] = ((unsigned long long)b << 32) | b;
+        }
+        const uint32_t nb = __float_as_uint(__double2float_rn(sh_M + ldexp(sB[c], sigma)));
+        row[d] = ((unsigned long long)nb << 32) | nb;
+      } else {
+        for (int j = 0; j < d; ++j) row[j] = 0ull;
+        const uint32_t nb = __float_as_uint((float)sh_dummy);
+        row[d] = ((unsigned long long)nb << 32) | nb;
+      }
+    }
+  } else {
+    __shared__ unsigned int sh_bmax_bits;
+    if (tid == 0) sh_bmax_bits = 0u;
+    __syncthreads();
+    for (int c = tid; c < k; c += nth) {
+      double B = 0.0;
+      for (int j = 0; j < d; ++j) {
+        const float cvj = __double2float_rn(__dsub_rn(a.mu[(size_t)c * d + j], (double)a.shift[j]));
+        a.ctil[(size_t)c * d + j] = cvj;
+        B = __dadd_rn(B, __dmul_rn((double)cvj, (double)cvj));
+      }
+      const float Bf = __double2float_ru(B);
+      a.cnorm[c] = Bf;
+      atomicMax(&sh_bmax_bits, __float_as_uint(Bf));  // B >= 0: bit order is value order
+    }
+    __syncthreads();
+    if (tid == 0) *a.gen_bmax = __uint_as_float(sh_bmax_bits);
+  }
+  __syncthreads();
+}
+
+constexpr int kRedCols = 32, kRedRows = 8;
+
+__global__ void __launch_bounds__(kRedCols * kRedRows) reduce_update_kernel(UpdateArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sB = reinterpret_cast<double*>(smraw);  // [k] for the fused-path tables
+  __shared__ unsigned long long s_lo[kRedRows][kRedCols];
+  __shared__ long long s_hi[kRedRows][kRedCols];
+  __shared__ bool s_last;
+  __shared__ double s_red[kRedCols * kRedRows];
+  if (a.ls->done) return;
+  const int cols = a.k * (a.d + 1);
+  const int col = blockIdx.x * kRedCols + threadIdx.x;
+  const int tid = threadIdx.y * kRedCols + threadIdx.x;
+  {
+    unsigned long long lo = 0ull;
+    long long hi = 0ll;
+    if (col < cols) {
+      for (int g = blockIdx.y * kRedRows + threadIdx.y; g < a.G; g += gridDim.y * kRedRows)
+        add128(lo, hi, a.partials[(size_t)g * cols + col]);
+    }
+    s_lo[threadIdx.y][threadIdx.x] = lo;
+    s_hi[threadIdx.y][threadIdx.x] = hi;
+    __syncthreads();
+    if (threadIdx.y == 0 && col < cols) {
+      unsigned long long tl = 0ull;
+      long long th = 0ll;
+      for (int r = 0; r < kRedRows; ++r) add128p(tl, th, s_lo[r][threadIdx.x], s_hi[r][threadIdx.x]);
+      long long* out = a.s128 + ((size_t)blockIdx.y * cols + col) * 2;
+      out[0] = (long long)tl;
+      out[1] = th;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned int t = atomicAdd(&a.ls->ticket, 1u);
+    s_last = (t == gridDim.x * gridDim.y - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+
+  // Last block: fixed-order totals, divide, error, stop test, next tables.
+  const int k = a.k, d = a.d, dp = d + 1, RB = gridDim.y;
+  const int nth = kRedCols * kRedRows;
+  int empty = 0;
+  for (int c = tid; c < k; c += nth) {
+    long long n = 0;
+    for (int rb = 0; rb < RB; ++rb) n += a.s128[((size_t)rb * cols + (size_t)c * dp + d) * 2];
+    a.counts[c] = n;
+    empty += (n == 0);
+  }
+  __syncthreads();
+  const int G0 = a.dc->G0;
+  double e2p = 0.0;
+  for (int q = tid; q < k * d; q += nth) {
+    const int c = q / d, j = q - c * d;
+    unsigned long long tl = 0ull;
+    long long th = 0ll;
+    for (int rb = 0; rb < RB; ++rb) {
+      const long long* v = a.s128 + ((size_t)rb * cols + (size_t)c * dp + j) * 2;
+      add128p(tl, th, (unsigned long long)v[0], v[1]);
+    }
+    const long long n = a.counts[c];
+    const double old = a.mu[q];
+    double nw = old;
+    if (n > 0) nw = __ddiv_rn(ldexp(i128_to_double((long long)tl, th), G0), (double)n);
+    const double df = __dsub_rn(nw, old);
+    e2p = __dadd_rn(e2p, __dmul_rn(df, df));
+    a.mu[q] = nw;
+  }
+  // fixed-order tree over threads
+  s_red[tid] = e2p;
+  __syncthreads();
+  for (int w = nth / 2; w > 0; w >>= 1) {
+    if (tid < w) s_red[tid] = __dadd_rn(s_red[tid], s_red[tid + w]);
+    __syncthreads();
+  }
+  __shared__ int s_empty;
+  if (tid == 0) s_empty = 0;
+  __syncthreads();
+  if (empty) atomicAdd(&s_empty, empty);
+  __syncthreads();
+  if (tid == 0) {
+    LoopState* ls = a.ls;
+    const double E2 = s_red[0];
+    const double E = sqrt(E2);
+    ls->E2 = E2;
+    ls->E = E;
+    ls->iter += 1;
+    ls->empty = s_empty;
+    const double esel = ls->e_mode == 1 ? E2 : E;
+    if (esel < ls->tol) { ls->converged = 1; ls->done = 1; }
+    if (ls->iter >= ls->max_iter) ls->done = 1;
+    ls->last_flagged = ls->flagged;
+    ls->last_fp64 = ls->fp64_decided;
+    ls->flagged = 0ull;
+    ls->fp64_decided = 0ull;
+    ls->ticket = 0u;
+  }
+  __syncthreads();
+  prepare_tables(a, sB);
+}
+
+__global__ void __launch_bounds__(256) prepare_kernel(UpdateArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  prepare_tables(a, reinterpret_cast<double*>(smraw));
+}
+
+__global__ void scan_range_kernel(const float* __restrict__ x, int64_t ld, int64_t n, int d,
+                                  unsigned int* mn_ord, unsigned int* mx_ord,
+                                  unsigned long long* nonfinite) {
+  const int j = blockIdx.y;
+  const float* row = x + (int64_t)j * ld;
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  unsigned long long bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = row[i];
+    if (!isfinite(v)) { ++bad; continue; }
+    const uint32_t o = ordered(v);
+    lo = min(lo, o);
+    hi = max(hi, o);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    lo = min(lo, __shfl_down_sync(0xffffffffu, lo, off));
+    hi = max(hi, __shfl_down_sync(0xffffffffu, hi, off));
+    bad += __shfl_down_sync(0xffffffffu, bad, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(mn_ord + j, lo);
+    atomicMax(mx_ord + j, hi);
+    if (bad) atomicAdd(nonfinite, bad);
+  }
+}
+
+// max_i of ||fl(x_i - s)||^2 evaluated exactly as the fused kernel does
+// (first term a product, then fused multiply-adds in coordinate order).
+__global__ void scan_amax_kernel(const float* __restrict__ x, int64_t ld, int64_t n, int d,
+                                 const float* __restrict__ shift, unsigned int* amax_bits) {
+  uint32_t best = 0u;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float t = __fsub_rn(x[i], shift[0]);
+    float A = __fmul_rn(t, t);
+    for (int j = 1; j < d; ++j) {
+      t = __fsub_rn(x[(int64_t)j * ld + i], shift[j]);
+      A = __fmaf_rn(t, t, A);
+    }
+    best = max(best, __float_as_uint(A));
+  }
+  for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_down_sync(0xffffffffu, best, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax_bits, best);
+}
+
+__global__ void aos_to_soa_kernel(const float* __restrict__ src, int64_t lds, int64_t n, int d,
+                                  float* __restrict__ dst, int64_t ldd) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int j = 0; j < d; ++j) dst[(int64_t)j * ldd + i] = src[i * lds + j];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_update(cudaStream_t st, const UpdateArgs& a) {
+  const int cols = a.k * (a.d + 1);
+  dim3 grid((cols + kRedCols - 1) / kRedCols, a.RB), block(kRedCols, kRedRows);
+  const size_t smem = (size_t)(a.fast ? a.k : 0) * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(reduce_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  reduce_update_kernel<<<grid, block, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare(cudaStream_t st, const UpdateArgs& a) {
+  const size_t smem = (size_t)(a.fast ? a.k : 0) * sizeof(double);
+  prepare_kernel<<<1, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_range(const float* x, int64_t ld, int64_t n, int d, float* mn, float* mx,
+                              unsigned long long* nonfinite, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(mn, 0xff, sizeof(float) * d, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mx, 0x00, sizeof(float) * d, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(nonfinite, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 1216);
+  dim3 grid((unsigned)std::max<int64_t>(blocks, 1), d);
+  scan_range_kernel<<<grid, 256, 0, st>>>(x, ld, n, d, reinterpret_cast<unsigned int*>(mn),
+                                          reinterpret_cast<unsigned int*>(mx), nonfinite);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_amax(const float* x, int64_t ld, int64_t n, int d, const float* shift,
+                             float* amax, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 1216);
+  scan_amax_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(
+      x, ld, n, d, shift, reinterpret_cast<unsigned int*>(amax));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aos_to_soa(const float* src, int64_t lds, int64_t n, int d, float* dst,
+                              int64_t ldd, cudaStream_t st) {
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  aos_to_soa_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(src, lds, n, d, dst, ldd);
+  return cudaGetLastError();
+}
+
+}  // namespace km

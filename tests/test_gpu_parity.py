@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Bar: labels and counts bit-exact; centroids within 1e-6 relative (per
+centroid, relative to max(||mu_ref,k||, RMS spread of X)); E within 1e-9
+absolute; iteration counts equal.  In lockstep tests both sides start every
+step from the same centroids (the oracle's), so labels must agree exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+CENT_REL = 1e-6
+E_ABS = 1e-9
+
+
+@pytest.fixture(scope="module")
+def km():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2405_12052_gb300 as m
+    m.build()
+    return m
+
+
+def spread(x):
+    xd = x.astype(np.float64)
+    return math.sqrt(((xd - xd.mean(axis=1, keepdims=True)) ** 2).sum(axis=0).mean())
+
+
+def assert_centroids_close(got, ref, x):
+    floor = spread(x)
+    for c in range(ref.shape[0]):
+        tol = CENT_REL * max(np.linalg.norm(ref[c]), floor, 1e-300)
+        assert np.linalg.norm(got[c] - ref[c]) <= tol, (c, got[c], ref[c])
+
+
+def lockstep(km, oracle, x, mu0, steps=1, **kw):
+    d, n = x.shape
+    k = mu0.shape[0]
+    g = km.KMeans(n, d, k, **kw)
+    g.set_points(x)
+    mu = np.array(mu0, dtype=np.float64)
+    for t in range(steps):
+        g.set_init(mu)
+        e, e2 = g.step()
+        z_ref, mu_ref, cnt_ref, e2_ref = oracle.step(x, mu)
+        z = g.labels()
+        assert np.array_equal(z, z_ref), (t, np.flatnonzero(z != z_ref)[:10])
+        assert np.array_equal(g.counts(), cnt_ref)
+        assert_centroids_close(g.centroids(), mu_ref, x)
+        assert abs(e - math.sqrt(e2_ref)) <= E_ABS and abs(e2 - e2_ref) <= max(E_ABS, 1e-12 * e2_ref)
+        mu = mu_ref
+    st = g.stats()
+    g.close()
+    return st
+
+
+def test_lockstep_plain_2d(km, oracle):
+    w = synth.workload("plain_2d_n1e5_k8")
+    st = lockstep(km, oracle, w["x"], w["mu0"], steps=8)
+    assert st["path"] == 1
+
+
+def test_full_run_plain_2d(km, oracle):
+    w = synth.workload("plain_2d_n1e5_k8")
+    ref = oracle.run(w["x"], w["mu0"], w["max_iter"], w["tol"])
+    for use_graph in (True, False):
+        g = km.KMeans(w["x"].shape[1], 2, w["k"], use_graph=use_graph)
+        g.set_points(w["x"])
+        g.set_init(w["mu0"])
+        r = g.run(w["max_iter"], w["tol"])
+        assert r["iters"] == ref["iters"] and r["converged"] == ref["converged"]
+        assert np.array_equal(r["labels"], ref["labels"])
+        assert np.array_equal(g.counts(), ref["counts"])
+        assert_centroids_close(r["centroids"], ref["centroids"], w["x"])
+        assert abs(r["E"] - ref["E"]) <= E_ABS
+        g.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 2047, 2048, 2049, 4101, 65537, 100003])
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_ragged_sizes(km, oracle, n, d):
+    k = min(n, 5)
+    x, _, _ = synth.iso_mixture(n, d, 4, sigma=1.0, box=5.0, seed=n + d)
+    mu0, _ = synth.init_distinct(x, k, seed=7)
+    lockstep(km, oracle, x, mu0, steps=2)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 31, 32, 33, 64, 100, 255, 256])
+def test_k_variants(km, oracle, k):
+    x, _, _ = synth.aniso_mixture(40_000, 3, 12, seed=k)
+    mu0, _ = synth.init_distinct(x, k, seed=k + 1)
+    lockstep(km, oracle, x, mu0, steps=2)
+
+
+@pytest.mark.parametrize("d,k", [(5, 3), (8, 40), (16, 7), (2, 300), (3, 257)])
+def test_generic_path(km, oracle, d, k):
+    x, _, _ = synth.iso_mixture(20_000, d, 6, sigma=1.5, box=5.0, seed=d * 100 + k)
+    mu0, _ = synth.init_distinct(x, k, seed=3)
+    st = lockstep(km, oracle, x, mu0, steps=2)
+    assert st["path"] == 2
+
+
+def test_exact_ties_go_to_lowest_index(km, oracle):
+    # integer grid points; centroids placed so many points sit exactly on
+    # bisectors, plus a duplicated centroid
+    g1 = np.arange(-6, 7, dtype=np.float32)
+    xx, yy = np.meshgrid(g1, g1)
+    x = np.stack([xx.ravel(), yy.ravel()]).astype(np.float32)
+    x = np.ascontiguousarray(np.tile(x, (1, 40)))
+    mu0 = np.array([[-2.0, 0.0], [2.0, 0.0], [0.0, 4.0], [0.0, 4.0], [0.0, -4.0]])
+    st = lockstep(km, oracle, x, mu0, steps=1)
+    assert st["flagged"] > 0 and st["fp64_decided"] > 0
+
+
+def test_empty_cluster_keeps_centre(km, oracle):
+    x, _, _ = synth.iso_mixture(30_000, 3, 3, sigma=1.0, box=5.0, seed=1)
+    mu0 = np.array([[0.0, 0.0, 0.0], [1.0, 1.0, 1.0], [500.0, 500.0, 500.0]])
+    lockstep(km, oracle, x, mu0, steps=2)
+    g = km.KMeans(x.shape[1], 3, 3)
+    g.set_points(x)
+    g.set_init(mu0)
+    g.step()
+    assert g.counts()[2] == 0 and np.array_equal(g.centroids()[2], mu0[2])
+    assert g.stats()["empty_clusters"] == 1
+
+
+def test_offset_cancellation(km, oracle):
+    # every coordinate offset by 1e4: the screen's shift keeps it exact
+    x, _, _ = synth.iso_mixture(200_000, 3, 16, sigma=1.0, box=20.0, seed=5, offset=1e4)
+    mu0, _ = synth.init_distinct(x, 16, seed=6)
+    st = lockstep(km, oracle, x, mu0, steps=3)
+    assert st["flagged"] < 0.01 * x.shape[1]
+
+
+def test_determinism_and_resume(km, oracle):
+    w = synth.workload("plain_2d_n1e5_k8")
+    outs = []
+    for _ in range(2):
+        g = km.KMeans(w["x"].shape[1], 2, 8)
+        g.set_points(w["x"])
+        g.set_init(w["mu0"])
+        outs.append(g.run(100, 1e-6))
+        g.close()
+    assert np.array_equal(outs[0]["labels"], outs[1]["labels"])
+    assert np.array_equal(outs[0]["centroids"], outs[1]["centroids"])
+    assert outs[0]["E"] == outs[1]["E"]
+    # stop after 3 steps, restart from the returned centroids: same final state
+    g = km.KMeans(w["x"].shape[1], 2, 8)
+    g.set_points(w["x"])
+    g.set_init(w["mu0"])
+    r1 = g.run(3, 1e-6)
+    g.set_init(r1["centroids"])
+    r2 = g.run(100, 1e-6)
+    assert r1["iters"] + r2["iters"] == outs[0]["iters"]
+    assert np.array_equal(r2["centroids"], outs[0]["centroids"])
+    assert np.array_equal(r2["labels"], outs[0]["labels"])
+
+
+def test_e_mode_squared(km, oracle):
+    w = synth.workload("plain_2d_n1e5_k8")
+    ref = oracle.run(w["x"], w["mu0"], 100, 1e-3, e_mode=1)
+    g = km.KMeans(w["x"].shape[1], 2, 8, e_mode="squared")
+    g.set_points(w["x"])
+    g.set_init(w["mu0"])
+    r = g.run(100, 1e-3)
+    assert r["iters"] == ref["iters"]
+    assert np.array_equal(r["labels"], ref["labels"])
+
+
+def test_device_borrow_and_aos(km, oracle):
+    import torch
+    x, _, _ = synth.aniso_mixture(50_001, 3, 8, seed=9)
+    mu0, _ = synth.init_distinct(x, 8, seed=10)
+    z_ref, mu_ref, _, _ = oracle.step(x, mu0)
+    for mode in ("borrow", "copy", "aos_host", "aos_dev"):
+        g = km.KMeans(x.shape[1], 3, 8)
+        if mode == "borrow":
+            t = torch.from_numpy(x).cuda()
+            g.set_points(t, borrow=True)
+        elif mode == "copy":
+            g.set_points(torch.from_numpy(x).cuda())
+        elif mode == "aos_host":
+            g.set_points(np.ascontiguousarray(x.T), layout="nxd")
+        else:
+            g.set_points(torch.from_numpy(np.ascontiguousarray(x.T)).cuda(), layout="nxd")
+        g.set_init(mu0)
+        g.step()
+        assert np.array_equal(g.labels(), z_ref), mode
+        assert_centroids_close(g.centroids(), mu_ref, x)
+        g.close()
+
+
+def test_errors_are_reported(km):
+    with pytest.raises(km.KMError) as ei:
+        km.KMeans(10, 2, 11)
+    assert ei.value.status == -1
+    g = km.KMeans(100, 2, 3)
+    with pytest.raises(km.KMError) as ei:
+        g.step()
+    assert ei.value.status == -4
+    x = np.zeros((2, 100), dtype=np.float32)
+    x[1, 17] = np.nan
+    with pytest.raises(km.KMError) as ei:
+        g.set_points(x)
+    assert ei.value.status == -6
+    with pytest.raises(km.KMError):
+        g.set_init(np.full((3, 2), np.inf))
+
+
+@pytest.mark.slow
+def test_full_scale_lockstep_3d_n1e8(km, oracle):
+    """The 1e8-point 3-D workload at full size, in the launch configuration the
+    benchmark times: one step from the k-means++ start, every label and count
+    compared with the oracle."""
+    w = synth.workload("plain_3d_n1e8_k32")
+    st = lockstep(km, oracle, w["x"], w["mu0"], steps=1)
+    assert st["path"] == 1
