@@ -158,6 +158,34 @@ km_status km_get_stats(km_ctx* ctx, km_stats* out);
 km_status km_device_buffers(km_ctx* ctx, const float** points, int64_t* ld_out,
                             int32_t** labels, double** centroids);
 
+/* One Lloyd step that allocates no memory (the paper has no counterpart; this
+ * entry point exists for callers that cannot call cudaMalloc, for example
+ * code running under an allocator that must not be entered after start-up, a
+ * real-time loop that forbids allocation, or a host framework that owns every
+ * device allocation).  Everything is caller-owned device memory: x (d x N SoA,
+ * row stride ld >= N, finite float32), mu_in (K x d doubles), and the outputs
+ * labels (N int32), mu_out (K x d doubles, may not alias mu_in), counts
+ * (K int64) and e2_out (one double: E^2 against mu_in).  Same results as
+ * km_step: exact labels (FP64 re-decision of near ties, ties to the lowest k),
+ * exact fixed-point sums, an empty cluster keeps its centre.
+ *
+ * Limits of the fixed scratch (a ~0.6 MB file-scope __device__ array that
+ * every device loading the library holds until exit): K*(d+1) <= 256 and
+ * N <= 304 * 2^19.  Larger sizes return KM_EINVAL with a message in errbuf
+ * (errbuf may be NULL; errlen is its size in bytes).
+ *
+ * The work is queued on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) and the call returns without synchronizing.  The first call on a
+ * device looks up the scratch array's device address (once per device, with
+ * that device current); make that first call before any stream capture.  All
+ * calls share the one scratch array, which keeps the last call's contents:
+ * calls that overlap on the GPU (different streams, or devices sharing the
+ * same context) race and give wrong results; serialize them. */
+km_status km_lloyd_step_noalloc(const float* x, int64_t ld, int64_t n, int32_t d, int32_t k,
+                                const double* mu_in, int32_t* labels, double* mu_out,
+                                int64_t* counts, double* e2_out, void* stream, char* errbuf,
+                                int32_t errlen);
+
 const char* km_last_error(const km_ctx* ctx);
 void km_destroy(km_ctx* ctx);
 

@@ -103,6 +103,8 @@ def lib(path: str | None = None):
     L.km_sync.restype = st
     L.km_stream.argtypes = [P]
     L.km_stream.restype = P
+    L.km_lloyd_step_noalloc.argtypes = [P, i64, i64, i32, i32, P, P, P, P, P, P, ctypes.c_char_p, i32]
+    L.km_lloyd_step_noalloc.restype = st
     L.km_last_error.argtypes = [P]
     L.km_last_error.restype = ctypes.c_char_p
     L.km_destroy.argtypes = [P]
