@@ -107,7 +107,7 @@ cudaError_t launch_assign(km_ctx* c) {
     a.x = c->x; a.ld = c->ld; a.n = c->n; a.k = c->k; a.kpad = c->kpad;
     a.tab2 = c->tab2; a.ctil = c->ctil4; a.mu = c->mu; a.ic = c->ic; a.dc = c->dc;
     a.ls = c->ls; a.labels = c->labels; a.partials = c->partials;
-    a.ntiles = (c->n + kTile - 1) / kTile;
+    a.ntiles = (c->n + kWarpTile - 1) / kWarpTile;
     e = launch_assign_fast(c->d, c->G, c->fast_smem, c->st, a);
   } else {
     GenericArgs a{};
@@ -192,17 +192,20 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
     KM_CUDA(c, cudaStreamCreate(&c->st));  // blocking: ordered after legacy-stream work
     c->own_stream = true;
   }
-  c->kpad = k + (k & 1);
+  c->kpad = (k + 3) / 4 * 4;  // the screen works on groups of 4 centroids
   c->fast = d <= kMaxDFast && k <= kMaxKFast;
   if (c->fast) {
     c->fast_smem = fast_smem_bytes(d, c->kpad, k);
     if (c->fast_smem > (size_t)p.sharedMemPerBlockOptin) c->fast = false;
   }
-  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t ntiles = (n + kWarpTile - 1) / kWarpTile;  // warp-tiles of 256 points
   if (c->fast) {
+    // one resident wave; each warp strides over warp-tiles, and no block
+    // takes more than 2^19 points (int64 per-block sums stay in range)
     const int bpsm = fast_blocks_per_sm(d, c->fast_smem);
-    int64_t g = std::min<int64_t>(ntiles, (int64_t)c->sms * bpsm);
-    g = std::max<int64_t>(g, (ntiles * kTile + kMaxPointsPerBlock - 1) / kMaxPointsPerBlock);
+    int64_t g = std::min<int64_t>((ntiles + kWarps - 1) / kWarps, (int64_t)c->sms * bpsm);
+    const int64_t tiles_per_block_max = kMaxPointsPerBlock / kWarpTile;
+    g = std::max<int64_t>(g, (ntiles + tiles_per_block_max - 1) / tiles_per_block_max);
     c->G = (int)std::max<int64_t>(g, 1);
   } else {
     int64_t g = std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)c->sms * 8);

@@ -150,52 +150,6 @@ __device__ int recheck_fast(const float* xo, const float* s, const float4* ctil,
 }
 
 template <int D>
-struct FastSmem {
-  static constexpr int DP = D + 1, WIN = 2 * D + 1;
-  unsigned long long* tab;  // [kpad][DP]
-  long long* acc;           // [kWarps][k][DP]
-  uint32_t* queue;          // [kQueueCap]
-  float4* ctil;             // [k]
-  uint32_t* win;            // [kWarps][k][WIN]
-  int* qn;                  // [4]: queue count, flagged, fp64
-  __device__ FastSmem(unsigned char* sm, int kpad, int k) {
-    tab = reinterpret_cast<unsigned long long*>(sm);
-    acc = reinterpret_cast<long long*>(tab + (size_t)kpad * DP);
-    queue = reinterpret_cast<uint32_t*>(acc + (size_t)kWarps * k * DP);
-    ctil = reinterpret_cast<float4*>(queue + kQueueCap);
-    win = reinterpret_cast<uint32_t*>(ctil + k);
-    qn = reinterpret_cast<int*>(win + (size_t)kWarps * k * WIN);
-  }
-};
-
-template <int D>
-__device__ __forceinline__ void flush_window(uint32_t* win, long long* acc, int k, int lane,
-                                             uint32_t bias_hi, uint32_t bias_lo) {
-  constexpr int DP = D + 1, WIN = 2 * D + 1;
-  __syncwarp();
-  // acc columns per centroid: 0..D-1 coordinate sums, D the count (the
-  // layout of the per-block partials); window slots: 0 the count, 1..D the
-  // high limbs, D+1..2D the low limbs.
-  for (int s = lane; s < k * DP; s += 32) {
-    int kk = s / DP, j = s - kk * DP;
-    const uint32_t* w = win + kk * WIN;
-    uint32_t c = w[0];
-    long long v;
-    if (j == D) {
-      v = (long long)c;
-    } else {
-      int hi = (int)(w[1 + j] - c * bias_hi);       // exact: |sum| < 2^30
-      int lo = (int)(w[1 + D + j] - c * bias_lo);
-      v = ((long long)hi << 22) + (long long)lo;
-    }
-    acc[s] += v;
-  }
-  __syncwarp();
-  for (int s = lane; s < k * WIN; s += 32) win[s] = 0u;
-  __syncwarp();
-}
-
-template <int D>
 __device__ __forceinline__ void accumulate_point(uint32_t* win, int kk, const float* xo,
                                                  float C_hi, float C_lo) {
   constexpr int WIN = 2 * D + 1;
@@ -210,46 +164,319 @@ __device__ __forceinline__ void accumulate_point(uint32_t* win, int kk, const fl
   }
 }
 
-// Drain the block's queue of flagged points.  Must be called by the whole
-// block, after a barrier that follows the last push.
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fsub2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long dup2(float v) { return pack2(v, v); }
+
+// Top-2 update of packed (value, index) floats with one new candidate.
+__device__ __forceinline__ void top2_one(float& m1, float& m2, float v) {
+  const float t = fmaxf(m1, v);
+  m1 = fminf(m1, v);
+  m2 = fminf(m2, t);
+}
+
+// Shared memory of the fused kernel.  Everything but the tables is private
+// to one warp: warps never wait for each other until the end.
 template <int D>
-__device__ void drain_queue(const FastArgs& a, FastSmem<D>& sm, const float* s, float C_hi,
-                            float C_lo, uint32_t bias_hi, uint32_t bias_lo, float B_max, float tau) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint32_t* win = sm.win + (size_t)warp * a.k * (2 * D + 1);
-  long long* acc = sm.acc + (size_t)warp * a.k * (D + 1);
-  flush_window<D>(win, acc, a.k, lane, bias_hi, bias_lo);
-  const int qn = min(sm.qn[0], kQueueCap);
-  int n64 = 0;
-  // Rounds of one entry per thread; the window is flushed every 16 rounds so
-  // that no bin receives more than 512 additions between flushes.
-  for (int r = 0, base = 0; base < qn; ++r, base += kThreads) {
-    const int q = base + tid;
-    if (q < qn) {
-      uint32_t loc = sm.queue[q];
-      int64_t tile = (int64_t)blockIdx.x + (int64_t)(loc >> 11) * gridDim.x;
-      int64_t i = tile * kTile + (loc & 2047u);
+struct FastSmem {
+  static constexpr int DP = D + 1, WIN = 2 * D + 1;
+  static constexpr int GS = (DP & 1) ? DP : DP + 1;  // float4 slots per group (odd: no bank conflicts)
+  unsigned long long* tab;  // [kpad][DP] screen table, packed (a, a) pairs (block)
+  long long* acc;           // [kWarps][k][DP] int64 totals
+  float4* ctil;             // [k] fp32 centroids for the re-check (block)
+  float4* gtab;             // [kpad/4][GS] screen table by group: slot j = coefficient j of the 4 centroids
+  float* xbuf;              // [kWarps][2][D][kWarpTile] double-buffered points
+  uint32_t* queue;          // [kWarps][kWarpQueue] flagged points
+  uint32_t* win;            // [kWarps][2][k+1][WIN] 32-bit windows per half-warp; bin k discards
+  int* cnt;                 // [2]: flagged, fp64-decided (block totals)
+  __device__ FastSmem(unsigned char* sm, int kpad, int k) {
+    tab = reinterpret_cast<unsigned long long*>(sm);
+    acc = reinterpret_cast<long long*>(tab + (size_t)kpad * DP);
+    ctil = reinterpret_cast<float4*>(acc + (size_t)kWarps * k * DP);
+    gtab = ctil + k;
+    xbuf = reinterpret_cast<float*>(gtab + (size_t)(kpad / 4) * GS);
+    queue = reinterpret_cast<uint32_t*>(xbuf + (size_t)kWarps * 2 * D * kWarpTile);
+    win = queue + (size_t)kWarps * kWarpQueue;
+    cnt = reinterpret_cast<int*>(win + (size_t)kWarps * 2 * (k + 1) * WIN);
+  }
+};
+
+// Flush both half-warp windows of a warp into its int64 totals.  acc
+// columns per centroid: 0..D-1 coordinate sums, D the count (the layout of
+// the per-block partials); window slots: 0 the count, 1..D the high limbs,
+// D+1..2D the low limbs.
+template <int D>
+__device__ __forceinline__ void flush_windows(uint32_t* wwarp, long long* acc, int k, int lane,
+                                              uint32_t bias_hi, uint32_t bias_lo) {
+  constexpr int DP = D + 1, WIN = 2 * D + 1;
+  const int half = (k + 1) * WIN;
+  __syncwarp();
+  for (int s = lane; s < k * DP; s += 32) {
+    const int kk = s / DP, j = s - kk * DP;
+    long long v = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t* w = wwarp + h * half + kk * WIN;
+      const uint32_t c = w[0];
+      if (j == D) {
+        v += (long long)c;
+      } else {
+        const int hi = (int)(w[1 + j] - c * bias_hi);  // exact: |sum| < 2^30
+        const int lo = (int)(w[1 + D + j] - c * bias_lo);
+        v += ((long long)hi << 22) + (long long)lo;
+      }
+    }
+    acc[s] += v;
+  }
+  __syncwarp();
+  for (int s = lane; s < 2 * half; s += 32) wwarp[s] = 0u;
+  __syncwarp();
+}
+
+// Asynchronous copy of this lane's two 16-byte chunks of each coordinate row
+// of warp-tile `base` (points base+4*lane.. and base+128+4*lane..) into a
+// warp buffer; chunks past N are zero-filled and read nothing past N.
+template <int D>
+__device__ __forceinline__ void prefetch_tile(const FastArgs& a, float* xb, int64_t base, int lane) {
+#pragma unroll
+  for (int g = 0; g < kNG; ++g) {
+    const int off = g * kGS + 4 * lane;
+    const int64_t i0 = base + off;
+    const int64_t rem = a.n - i0;
+    const int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const float* src = a.x + (int64_t)j * a.ld + (bytes ? i0 : 0);
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(xb + j * kWarpTile + off);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes));
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Re-decide the points in this warp's queue (warp-level: lanes take
+// entries; windows are flushed every 32 rounds, <= 512 additions per bin).
+template <int D>
+__device__ void drain_warp_queue(const FastArgs& a, FastSmem<D>& sm, uint32_t* q, int qn, int wid,
+                                 int wtot, uint32_t* wwarp, uint32_t* wmine, long long* acc, int lane,
+                                 const float* s, const DataConst& dc, float B_max, float tau, int& n64) {
+  flush_windows<D>(wwarp, acc, a.k, lane, dc.bits_C_hi, dc.bits_C_lo);
+  for (int r = 0, b = 0; b < qn; ++r, b += 32) {
+    const int e = b + lane;
+    if (e < qn) {
+      const uint32_t loc = q[e];
+      const int64_t tile = (int64_t)wid + (int64_t)(loc >> 8) * wtot;
+      const int64_t i = tile * kWarpTile + (loc & 255u);
       float xo[D];
 #pragma unroll
       for (int j = 0; j < D; ++j) xo[j] = a.x[(int64_t)j * a.ld + i];
       bool used64;
-      int kk = recheck_fast<D>(xo, s, sm.ctil, a.mu, a.k, B_max, tau, used64);
+      const int kk = recheck_fast<D>(xo, s, sm.ctil, a.mu, a.k, B_max, tau, used64);
       n64 += used64 ? 1 : 0;
       a.labels[i] = kk;
-      accumulate_point<D>(win, kk, xo, C_hi, C_lo);
+      accumulate_point<D>(wmine, kk, xo, dc.C_hi, dc.C_lo);
     }
-    if ((r & 15) == 15) flush_window<D>(win, acc, a.k, lane, bias_hi, bias_lo);
+    if ((r & 31) == 31) flush_windows<D>(wwarp, acc, a.k, lane, dc.bits_C_hi, dc.bits_C_lo);
   }
-  flush_window<D>(win, acc, a.k, lane, bias_hi, bias_lo);
-  if (n64) atomicAdd(&sm.qn[2], n64);
-  __syncthreads();
-  if (tid == 0) { sm.qn[1] += qn; sm.qn[0] = 0; }
-  __syncthreads();
+  flush_windows<D>(wwarp, acc, a.k, lane, dc.bits_C_hi, dc.bits_C_lo);
+}
+
+// Per-launch constants of the fused kernel, in registers.
+struct FastCtx {
+  uint32_t mul, L, kmask, bitsM_low;
+  float thr_c0, thr_cA2, tau;
+  unsigned long long chi2, clo2;
+  int k, kpad;
+};
+
+// One warp-tile: grouped screen, exact recompute of the winning group, flags,
+// labels and exact sums.  FULL: all 256 points exist (no bounds checks).
+template <int D, bool FULL>
+__device__ __forceinline__ void process_tile(const FastArgs& a, FastSmem<D>& sm, const FastCtx& cx,
+                                             const unsigned long long* s2, const float* xcur, int64_t base,
+                                             int m, int lane, uint32_t* wmine, uint32_t* q, int& qn) {
+  constexpr int DP = D + 1, WIN = 2 * D + 1, GS = FastSmem<D>::GS;
+  // this lane's points: base + g*128 + 4*lane + q, g in {0,1}, q in 0..3;
+  // pair pp holds points 2pp, 2pp+1.  X = x~ = fl(x - s) per pair.
+  unsigned long long X[D][kPts / 2];
+#pragma unroll
+  for (int g = 0; g < kNG; ++g)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(xcur + j * kWarpTile + g * kGS + 4 * lane);
+      X[j][2 * g] = fsub2(v.x, s2[j]);
+      X[j][2 * g + 1] = fsub2(v.y, s2[j]);
+    }
+  // A = ||x~||^2 exactly as the data scan that bounds it: x0*x0, then FMAs.
+  float Ap[kPts];
+#pragma unroll
+  for (int pp = 0; pp < kPts / 2; ++pp) {
+    unsigned long long a2 = ffma2(X[0][pp], X[0][pp], 0ull);
+#pragma unroll
+    for (int j = 1; j < D; ++j) a2 = ffma2(X[j][pp], X[j][pp], a2);
+    unpack2(a2, Ap[2 * pp], Ap[2 * pp + 1]);
+  }
+
+  // Grouped screen: per group of 4 centroids only the group minimum of the
+  // raw r values is kept; the top-2 runs over groups, packed with the
+  // group's first index.
+  float m1[kPts], m2[kPts];
+#pragma unroll
+  for (int p = 0; p < kPts; ++p) { m1[p] = 3.0e38f; m2[p] = 3.0e38f; }
+#pragma unroll 1
+  for (int g4 = 0; g4 < cx.kpad; g4 += 4) {
+    const unsigned long long* tr = sm.tab + (size_t)g4 * DP;
+    unsigned long long T[4][DP];
+    if constexpr (D <= 3) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < DP; ++j) T[c][j] = tr[c * DP + j];
+    }
+#pragma unroll
+    for (int pp = 0; pp < kPts / 2; ++pp) {
+      if constexpr (D > 3) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int j = 0; j < DP; ++j) T[c][j] = tr[c * DP + j];
+      }
+      float v0[4], v1[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        unsigned long long r = T[c][D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) r = ffma2(X[j][pp], T[c][j], r);
+        unpack2(r, v0[c], v1[c]);
+      }
+      const float gm0 = fminf(fmin3(v0[0], v0[1], v0[2]), v0[3]);
+      const float gm1 = fminf(fmin3(v1[0], v1[1], v1[2]), v1[3]);
+      top2_one(m1[2 * pp], m2[2 * pp], __uint_as_float(imad(__float_as_uint(gm0), cx.mul, (uint32_t)g4)));
+      top2_one(m1[2 * pp + 1], m2[2 * pp + 1], __uint_as_float(imad(__float_as_uint(gm1), cx.mul, (uint32_t)g4)));
+    }
+  }
+
+  // Epilogue: the winning group is recomputed exactly (the same FMA chain,
+  // two centroids per FFMA2) for the winner's index and the group's own
+  // second value; flags and labels follow.
+  int lab[kPts];
+  uint32_t fbits = 0u, dbits = 0u;  // flagged; not accumulated here
+#pragma unroll
+  for (int p = 0; p < kPts; ++p) {
+    float xt[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float lo, hi;
+      unpack2(X[j][p >> 1], lo, hi);
+      xt[j] = (p & 1) ? hi : lo;
+    }
+    const uint32_t gsel = __float_as_uint(m1[p]) & cx.kmask;
+    const ulonglong2* gt = reinterpret_cast<const ulonglong2*>(sm.gtab + (size_t)(gsel >> 2) * GS);
+    const ulonglong2 nv = gt[D];
+    unsigned long long rA = nv.x, rB = nv.y;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const ulonglong2 cv = gt[j];
+      const unsigned long long xx = dup2(xt[j]);
+      rA = ffma2(xx, cv.x, rA);
+      rB = ffma2(xx, cv.y, rB);
+    }
+    float r0, r1, r2, r3;
+    unpack2(rA, r0, r1);
+    unpack2(rB, r2, r3);
+    const float w0 = __uint_as_float(imad(__float_as_uint(r0), cx.mul, gsel));
+    const float w1_ = __uint_as_float(imad(__float_as_uint(r1), cx.mul, gsel + 1u));
+    const float w2_ = __uint_as_float(imad(__float_as_uint(r2), cx.mul, gsel + 2u));
+    const float w3 = __uint_as_float(imad(__float_as_uint(r3), cx.mul, gsel + 3u));
+    const float lo01 = fminf(w0, w1_), hi01 = fmaxf(w0, w1_);
+    const float lo23 = fminf(w2_, w3), hi23 = fmaxf(w2_, w3);
+    const float best = fminf(lo01, lo23);
+    const float sec = fminf(fmin3(fmaxf(lo01, lo23), hi01, hi23), m2[p]);
+    const uint32_t u1 = __float_as_uint(best), u2 = __float_as_uint(sec);
+    lab[p] = (int)(u1 & cx.kmask);
+    const uint32_t b1 = u1 >> cx.L, b2 = u2 >> cx.L;
+    const float gap = (float)(int)(b2 - b1);
+    const float w2u = (float)(int)(b2 - cx.bitsM_low);
+    const float T = cx.thr_c0 + Ap[p] * cx.thr_cA2 + cx.tau * w2u;
+    // a label outside 0..K-1 (only a padding centroid could give one) is
+    // never trusted: the point goes to the re-check
+    bool f = !(gap > T) || lab[p] >= cx.k;
+    bool dis = f;
+    if constexpr (!FULL) {
+      const bool valid = base + (p >> 2) * kGS + 4 * lane + (p & 3) < a.n;
+      f = f && valid;
+      dis = dis || !valid;
+    }
+    fbits |= (f ? 1u : 0u) << p;
+    dbits |= (dis ? 1u : 0u) << p;
+  }
+  if (__any_sync(0xffffffffu, fbits != 0u)) {
+#pragma unroll
+    for (int p = 0; p < kPts; ++p) {
+      const bool f = (fbits >> p) & 1u;
+      const unsigned bm = __ballot_sync(0xffffffffu, f);
+      if (f) {
+        const int off = (p >> 2) * kGS + 4 * lane + (p & 3);
+        q[qn + __popc(bm & ((1u << lane) - 1u))] = (uint32_t)(m << 8) | (uint32_t)off;
+      }
+      qn += __popc(bm);
+    }
+  }
+  // labels (flagged points are overwritten by the re-check)
+#pragma unroll
+  for (int g = 0; g < kNG; ++g) {
+    const int64_t i0 = base + g * kGS + 4 * lane;
+    if constexpr (FULL) {
+      *reinterpret_cast<int4*>(a.labels + i0) = make_int4(lab[4 * g], lab[4 * g + 1], lab[4 * g + 2], lab[4 * g + 3]);
+    } else {
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) if (i0 + qq < a.n) a.labels[i0 + qq] = lab[4 * g + qq];
+    }
+  }
+  // Exact sums: limb splits on FADD2 pairs, then 32-bit shared atomics into
+  // this half-warp's window; flagged and padding points go to the discard bin k.
+#pragma unroll
+  for (int g = 0; g < kNG; ++g)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int p0 = 4 * g + 2 * h;
+      uint32_t bh[D][2], bl[D][2];
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const unsigned long long xv =
+            *reinterpret_cast<const unsigned long long*>(xcur + j * kWarpTile + g * kGS + 4 * lane + 2 * h);
+        const unsigned long long t = fadd2(xv, cx.chi2);
+        const unsigned long long hh = fsub2(t, cx.chi2);
+        const unsigned long long r = fsub2(xv, hh);
+        const unsigned long long t2 = fadd2(r, cx.clo2);
+        asm("mov.b64 {%0, %1}, %2;" : "=r"(bh[j][0]), "=r"(bh[j][1]) : "l"(t));
+        asm("mov.b64 {%0, %1}, %2;" : "=r"(bl[j][0]), "=r"(bl[j][1]) : "l"(t2));
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int bin = ((dbits >> (p0 + e)) & 1u) ? cx.k : lab[p0 + e];
+        uint32_t* wb = wmine + bin * WIN;
+        atomicAdd(&wb[0], 1u);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          atomicAdd(&wb[1 + j], bh[j][e]);
+          atomicAdd(&wb[1 + D + j], bl[j][e]);
+        }
+      }
+    }
 }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads, 2) assign_fast_kernel(FastArgs a) {
-  constexpr int DP = D + 1;
+__global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs a) {
+  constexpr int DP = D + 1, WIN = 2 * D + 1, GS = FastSmem<D>::GS;
   extern __shared__ __align__(16) unsigned char smraw[];
   if (a.ls->done) return;  // the loop already stopped (graph-driven runs)
   FastSmem<D> sm(smraw, a.kpad, a.k);
@@ -259,157 +486,83 @@ __global__ void __launch_bounds__(kThreads, 2) assign_fast_kernel(FastArgs a) {
   const IterConst ic = *a.ic;
   const DataConst dc = *a.dc;
   float s[D];
+  unsigned long long s2[D];
 #pragma unroll
-  for (int j = 0; j < D; ++j) s[j] = dc.s[j];
+  for (int j = 0; j < D; ++j) { s[j] = dc.s[j]; s2[j] = dup2(dc.s[j]); }
 
-  for (int q = tid; q < kpad * DP; q += kThreads) sm.tab[q] = a.tab2[q];
-  for (int q = tid; q < k; q += kThreads) sm.ctil[q] = a.ctil[q];
-  for (int q = tid; q < kWarps * k * DP; q += kThreads) sm.acc[q] = 0;
-  for (int q = tid; q < kWarps * k * (2 * D + 1); q += kThreads) sm.win[q] = 0u;
-  if (tid < 4) sm.qn[tid] = 0;
+  uint32_t* wwarp = sm.win + (size_t)warp * 2 * (k + 1) * WIN;
+  uint32_t* wmine = wwarp + (size_t)(lane >> 4) * (k + 1) * WIN;
+  long long* acc = sm.acc + (size_t)warp * k * DP;
+  uint32_t* q = sm.queue + (size_t)warp * kWarpQueue;
+  float* xb = sm.xbuf + (size_t)warp * 2 * D * kWarpTile;
+  const int wid = blockIdx.x * kWarps + warp;  // this warp's first tile
+  const int wtot = gridDim.x * kWarps;         // tile stride
+  const int ntiles = (int)a.ntiles;            // < 2^31 (N < 2^39)
+  if (wid < ntiles) prefetch_tile<D>(a, xb, (int64_t)wid * kWarpTile, lane);
+
+  for (int q2 = tid; q2 < kpad * DP; q2 += kThreads) {
+    const unsigned long long v = a.tab2[q2];
+    sm.tab[q2] = v;
+    const int c = q2 / DP, j = q2 - c * DP;
+    reinterpret_cast<float*>(sm.gtab + (size_t)(c >> 2) * GS + j)[c & 3] = __uint_as_float((uint32_t)v);
+  }
+  for (int q2 = tid; q2 < k; q2 += kThreads) sm.ctil[q2] = a.ctil[q2];
+  for (int q2 = tid; q2 < kWarps * k * DP; q2 += kThreads) sm.acc[q2] = 0;
+  for (int q2 = tid; q2 < kWarps * 2 * (k + 1) * WIN; q2 += kThreads) sm.win[q2] = 0u;
+  if (tid < 2) sm.cnt[tid] = 0;
   __syncthreads();
 
-  uint32_t* win = sm.win + (size_t)warp * k * (2 * D + 1);
-  long long* acc = sm.acc + (size_t)warp * k * DP;
-  const uint32_t mul = ic.mul, L = (uint32_t)ic.L, kmask = mul - 1u;
-  int since_flush = 0;
-  int64_t local_tile = 0;
+  FastCtx cx;
+  cx.mul = ic.mul; cx.L = (uint32_t)ic.L; cx.kmask = ic.mul - 1u; cx.bitsM_low = ic.bitsM_low;
+  cx.thr_c0 = ic.thr_c0; cx.thr_cA2 = ic.thr_cA + ic.tau * ic.G; cx.tau = ic.tau;
+  cx.chi2 = dup2(dc.C_hi); cx.clo2 = dup2(dc.C_lo);
+  cx.k = k; cx.kpad = kpad;
+  int qn = 0, nflag = 0, n64 = 0, since_flush = 0;
+  int m = 0;  // this warp's local tile counter
 
-  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++local_tile) {
-    const int64_t base = tile * kTile;
-    const bool full = base + kTile <= a.n;
-    float xo[D][kPts];
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      const int64_t i0 = base + g * (kTile / 2) + 4 * tid;
-      if (full) {
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          float4 v = ld_stream4(a.x + (int64_t)j * a.ld + i0);
-          xo[j][4 * g + 0] = v.x; xo[j][4 * g + 1] = v.y;
-          xo[j][4 * g + 2] = v.z; xo[j][4 * g + 3] = v.w;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int64_t i = i0 + q;
-#pragma unroll
-          for (int j = 0; j < D; ++j) xo[j][4 * g + q] = (i < a.n) ? a.x[(int64_t)j * a.ld + i] : s[j];
-        }
-      }
-    }
-    // Shifted coordinates (x~ = fl(x - s)) and A = ||x~||^2 in the same
-    // expression as the data scan that bounds it.
-    float Ap[kPts];
-    unsigned long long X[D][kPts / 2];
-#pragma unroll
-    for (int p = 0; p < kPts; p += 2) {
-      float t0[D], t1[D];
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        t0[j] = __fsub_rn(xo[j][p], s[j]);
-        t1[j] = __fsub_rn(xo[j][p + 1], s[j]);
-        X[j][p / 2] = pack2(t0[j], t1[j]);
-      }
-      float a0 = __fmul_rn(t0[0], t0[0]), a1 = __fmul_rn(t1[0], t1[0]);
-#pragma unroll
-      for (int j = 1; j < D; ++j) { a0 = __fmaf_rn(t0[j], t0[j], a0); a1 = __fmaf_rn(t1[j], t1[j], a1); }
-      Ap[p] = a0; Ap[p + 1] = a1;
-    }
-    // Screen: top-2 of packed (r, k) over all centroids.
-    float m1[kPts], m2[kPts];
-#pragma unroll
-    for (int p = 0; p < kPts; ++p) { m1[p] = 3.0e38f; m2[p] = 3.0e38f; }
-#pragma unroll 2
-    for (int kp = 0; kp < kpad; kp += 2) {
-      unsigned long long ta[DP], tb[DP];
-      const unsigned long long* ra = sm.tab + (size_t)kp * DP;
-#pragma unroll
-      for (int j = 0; j < DP; ++j) { ta[j] = ra[j]; tb[j] = ra[DP + j]; }
-#pragma unroll
-      for (int pp = 0; pp < kPts / 2; ++pp) {
-        unsigned long long rA = ta[D], rB = tb[D];
-#pragma unroll
-        for (int j = 0; j < D; ++j) { rA = ffma2(X[j][pp], ta[j], rA); rB = ffma2(X[j][pp], tb[j], rB); }
-        float a0, a1, b0, b1;
-        unpack2(rA, a0, a1);
-        unpack2(rB, b0, b1);
-        const float pa0 = __uint_as_float(imad(__float_as_uint(a0), mul, (uint32_t)kp));
-        const float pa1 = __uint_as_float(imad(__float_as_uint(a1), mul, (uint32_t)kp));
-        const float pb0 = __uint_as_float(imad(__float_as_uint(b0), mul, (uint32_t)kp + 1u));
-        const float pb1 = __uint_as_float(imad(__float_as_uint(b1), mul, (uint32_t)kp + 1u));
-        top2_pair(m1[2 * pp], m2[2 * pp], pa0, pb0);
-        top2_pair(m1[2 * pp + 1], m2[2 * pp + 1], pa1, pb1);
-      }
-    }
-    // Epilogue: labels, flags, accumulation.
-    int lab[kPts];
-    bool flg[kPts];
-#pragma unroll
-    for (int p = 0; p < kPts; ++p) {
-      const int64_t i = base + (p >> 2) * (kTile / 2) + 4 * tid + (p & 3);
-      const bool valid = full || i < a.n;
-      const uint32_t u1 = __float_as_uint(m1[p]), u2 = __float_as_uint(m2[p]);
-      lab[p] = (int)(u1 & kmask);
-      const uint32_t b1 = u1 >> L, b2 = u2 >> L;
-      const float gap = (float)(b2 - b1);
-      const float w2u = (float)(int)(b2 - ic.bitsM_low);
-      const float T = ic.thr_c0 + Ap[p] * ic.thr_cA + ic.tau * fmaxf(0.f, w2u + Ap[p] * ic.G);
-      // a label outside 0..K-1 (only the padding centroid could give one) is
-      // never trusted: the point goes to the re-check
-      flg[p] = valid && (!(gap > T) || lab[p] >= k);
-      if (flg[p]) {
-        const int q = atomicAdd(&sm.qn[0], 1);
-        if (q < kQueueCap)
-          sm.queue[q] = (uint32_t)(local_tile << 11) | (uint32_t)((p >> 2) * (kTile / 2) + 4 * tid + (p & 3));
-        else
-          a.ls->error = 1;  // cannot happen: the queue is drained above kQueueCap - kTile
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      const int64_t i0 = base + g * (kTile / 2) + 4 * tid;
-      if (full) {
-        *reinterpret_cast<int4*>(a.labels + i0) =
-            make_int4(lab[4 * g], lab[4 * g + 1], lab[4 * g + 2], lab[4 * g + 3]);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) if (i0 + q < a.n) a.labels[i0 + q] = lab[4 * g + q];
-      }
-    }
-#pragma unroll
-    for (int p = 0; p < kPts; ++p) {
-      const int64_t i = base + (p >> 2) * (kTile / 2) + 4 * tid + (p & 3);
-      if ((full || i < a.n) && !flg[p]) {
-        float xp[D];
-#pragma unroll
-        for (int j = 0; j < D; ++j) xp[j] = xo[j][p];
-        accumulate_point<D>(win, lab[p], xp, dc.C_hi, dc.C_lo);
-      }
-    }
-    if (++since_flush == 2) {
-      flush_window<D>(win, acc, k, lane, dc.bits_C_hi, dc.bits_C_lo);
+  for (int tile = wid; tile < ntiles; tile += wtot, ++m) {
+    const int64_t base = (int64_t)tile * kWarpTile;
+    const float* xcur = xb + (m & 1) * D * kWarpTile;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (tile + wtot < ntiles)
+      prefetch_tile<D>(a, xb + ((m + 1) & 1) * D * kWarpTile, (int64_t)(tile + wtot) * kWarpTile, lane);
+    if (base + kWarpTile <= a.n)
+      process_tile<D, true>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
+    else
+      process_tile<D, false>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
+    if (++since_flush == 4) {  // 16 lanes x 8 points x 4 tiles: <= 512 additions per half-warp bin
+      flush_windows<D>(wwarp, acc, k, lane, dc.bits_C_hi, dc.bits_C_lo);
       since_flush = 0;
     }
-    __syncthreads();
-    if (sm.qn[0] > kQueueCap - kTile) {
-      drain_queue<D>(a, sm, s, dc.C_hi, dc.C_lo, dc.bits_C_hi, dc.bits_C_lo, ic.B_max, ic.tau);
+    if (qn > kWarpQueue - kWarpTile) {
+      __syncwarp();
+      drain_warp_queue<D>(a, sm, q, qn, wid, wtot, wwarp, wmine, acc, lane, s, dc, ic.B_max, ic.tau, n64);
+      nflag += qn;
+      qn = 0;
+      since_flush = 0;
     }
   }
-  flush_window<D>(win, acc, k, lane, dc.bits_C_hi, dc.bits_C_lo);
-  __syncthreads();
-  if (sm.qn[0] > 0) drain_queue<D>(a, sm, s, dc.C_hi, dc.C_lo, dc.bits_C_hi, dc.bits_C_lo, ic.B_max, ic.tau);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+  if (qn > 0) {
+    drain_warp_queue<D>(a, sm, q, qn, wid, wtot, wwarp, wmine, acc, lane, s, dc, ic.B_max, ic.tau, n64);
+    nflag += qn;
+  } else {
+    flush_windows<D>(wwarp, acc, k, lane, dc.bits_C_hi, dc.bits_C_lo);
+  }
+  if (lane == 0 && nflag) atomicAdd(&sm.cnt[0], nflag);
+  if (n64) atomicAdd(&sm.cnt[1], n64);
   __syncthreads();
   long long* out = a.partials + (size_t)blockIdx.x * k * DP;
-  for (int q = tid; q < k * DP; q += kThreads) {
+  for (int q2 = tid; q2 < k * DP; q2 += kThreads) {
     long long v = 0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) v += sm.acc[(size_t)w * k * DP + q];
-    out[q] = v;
+    for (int w = 0; w < kWarps; ++w) v += sm.acc[(size_t)w * k * DP + q2];
+    out[q2] = v;
   }
   if (tid == 0) {
-    if (sm.qn[1]) atomicAdd(&a.ls->flagged, (unsigned long long)sm.qn[1]);
-    if (sm.qn[2]) atomicAdd(&a.ls->fp64_decided, (unsigned long long)sm.qn[2]);
+    if (sm.cnt[0]) atomicAdd(&a.ls->flagged, (unsigned long long)sm.cnt[0]);
+    if (sm.cnt[1]) atomicAdd(&a.ls->fp64_decided, (unsigned long long)sm.cnt[1]);
   }
 }
 
@@ -489,9 +642,10 @@ __global__ void __launch_bounds__(kThreads) assign_generic_kernel(GenericArgs a)
 }  // namespace
 
 size_t fast_smem_bytes(int d, int kpad, int k) {
-  const int dp = d + 1, win = 2 * d + 1;
-  size_t b = (size_t)kpad * dp * 8 + (size_t)kWarps * k * dp * 8 + (size_t)kQueueCap * 4 +
-             (size_t)k * 16 + (size_t)kWarps * k * win * 4 + 16;
+  const int dp = d + 1, win = 2 * d + 1, gs = (dp & 1) ? dp : dp + 1;
+  size_t b = (size_t)kpad * dp * 8 + (size_t)kWarps * k * dp * 8 + (size_t)k * 16 + (size_t)(kpad / 4) * gs * 16 +
+             (size_t)kWarps * 2 * d * kWarpTile * 4 + (size_t)kWarps * kWarpQueue * 4 +
+             (size_t)kWarps * 2 * (k + 1) * win * 4 + 16;
   return (b + 15) & ~size_t(15);
 }
 

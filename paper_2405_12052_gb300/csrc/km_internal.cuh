@@ -37,9 +37,18 @@ constexpr int kMaxDFast = 4;        // fused FFMA2 kernel: d <= 4
 constexpr int kMaxKFast = 256;      // and K <= 256 (index in <= 8 low bits)
 constexpr int kThreads = 256;       // threads per block of the assign kernels
 constexpr int kWarps = kThreads / 32;
-constexpr int kPts = 8;             // points per thread per tile (fused kernel)
-constexpr int kTile = kThreads * kPts;  // 2048 points per block per tile
-constexpr int kQueueCap = 6144;     // flagged points queued per block (drained above 4096)
+#ifndef KM_PTS
+#define KM_PTS 8
+#endif
+constexpr int kPts = KM_PTS;        // points per lane per warp-tile (fused kernel): 4 or 8
+constexpr int kNG = kPts / 4;       // groups of 4 consecutive points per lane
+constexpr int kGS = 128;            // points between a lane's groups (32 lanes x 4)
+constexpr int kWarpTile = 32 * kPts;  // points per warp-tile
+static_assert(kPts == 4 || kPts == 8, "points per lane");
+#ifndef KM_MINB
+#define KM_MINB 2                   // resident blocks per SM the fused kernel is compiled for
+#endif
+constexpr int kWarpQueue = 320;     // flagged points queued per warp (drained above 64)
 constexpr int64_t kMaxPointsPerBlock = int64_t(1) << 19;
 
 // Per-dataset constants, fixed by km_set_points.
