@@ -148,7 +148,9 @@ typedef struct km_stats {
   int64_t flagged;        /* points re-checked past the FP32 screen in the last step */
   int64_t fp64_decided;   /* of those, points decided in FP64 */
   int32_t empty_clusters; /* clusters with no points in the last step */
-  int32_t path;           /* 1: fused FFMA2 kernel (d <= 4, K <= 256); 2: generic kernel */
+  int64_t overflowed;     /* tensor-core path: points whose candidate list overflowed (all K re-ranked) */
+  int32_t path;           /* 1: fused FFMA2 kernel (d <= 4, K <= 256); 2: generic kernel;
+                             3: tcgen05 BF16 GEMM-form kernel (d = 64, K <= 1024) */
 } km_stats;
 km_status km_get_stats(km_ctx* ctx, km_stats* out);
 

@@ -46,7 +46,7 @@ class _Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("e", ctypes.c_double),
                 ("e2", ctypes.c_double), ("flagged", ctypes.c_int64),
                 ("fp64_decided", ctypes.c_int64), ("empty_clusters", ctypes.c_int32),
-                ("path", ctypes.c_int32)]
+                ("overflowed", ctypes.c_int64), ("path", ctypes.c_int32)]
 
 
 _lib = None

@@ -47,6 +47,24 @@ struct km_ctx {
   float* scan = nullptr;  // [2d] min/max + [1] amax
   unsigned long long* scan_bad = nullptr;
   size_t fast_smem = 0;
+  int path = 0;  // 1 fused (d <= 4, K <= 256), 2 generic, 3 tensor cores (d = 64, K <= 1024)
+  // tensor-core path
+  void* xb = nullptr;
+  float* xa_pt = nullptr;
+  float* xaos = nullptr;
+  void* cbf = nullptr;
+  float* nprime = nullptr;
+  GemmConst* gc = nullptr;
+  // sorted mean calculation
+  unsigned long long* ms_counts = nullptr;
+  int64_t* ms_offsets = nullptr;
+  int* ms_cfirst = nullptr;
+  unsigned long long* ms_cursor = nullptr;
+  int4* ms_chunks = nullptr;
+  int* ms_nchunks = nullptr;
+  long long* ms_chunk_sums = nullptr;
+  int32_t* ms_perm = nullptr;
+  int ms_max_chunks = 0;
   float A_max = 0.f;
   int G0 = 0;
   // loop
@@ -81,7 +99,9 @@ void free_all(km_ctx* c) {
   c->graph = nullptr;
   void* bufs[] = {c->x_own, c->labels, c->mu, c->counts, c->partials, c->s128, c->tab2,
                   c->ctil4, c->ctil, c->cnorm, c->shift, c->gen_bmax, c->dc, c->ic, c->ls,
-                  c->scan, c->scan_bad};
+                  c->scan, c->scan_bad, c->xb, c->xa_pt, c->xaos, c->cbf, c->nprime, c->gc,
+                  c->ms_counts, c->ms_offsets, c->ms_cfirst, c->ms_cursor, c->ms_chunks, c->ms_nchunks,
+                  c->ms_chunk_sums, c->ms_perm};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -99,9 +119,39 @@ UpdateArgs update_args(km_ctx* c) {
   return u;
 }
 
-// Reassignment + per-block sums (one kernel).
+GemmPrepArgs gemm_prep_args(km_ctx* c) {
+  GemmPrepArgs g{};
+  g.mu = c->mu; g.shift = c->shift; g.k = c->k; g.kpad = c->kpad;
+  g.cb = c->cbf; g.nprime = c->nprime; g.ctil = c->ctil; g.gc = c->gc;
+  g.A_max = c->A_max; g.tie_rel = c->opt.tie_rel; g.ls = c->ls;
+  return g;
+}
+
+MsortArgs msort_args(km_ctx* c) {
+  MsortArgs m{};
+  m.labels = c->labels; m.n = c->n; m.k = c->k; m.d = c->d; m.xa = c->xaos; m.dc = c->dc;
+  m.counts_u = c->ms_counts; m.offsets = c->ms_offsets; m.cfirst = c->ms_cfirst; m.cursor = c->ms_cursor;
+  m.chunks = c->ms_chunks; m.nchunks = c->ms_nchunks; m.max_chunks = c->ms_max_chunks;
+  m.chunk_sums = c->ms_chunk_sums; m.perm = c->ms_perm; m.mu = c->mu; m.counts = c->counts; m.ls = c->ls;
+  return m;
+}
+
+// Screen tables from the current centroids.
+cudaError_t launch_tables(km_ctx* c) {
+  if (c->path == 3) return launch_gemm_prepare(c->st, gemm_prep_args(c));
+  return launch_prepare(c->st, update_args(c));
+}
+
+// Reassignment (+ per-block sums on paths 1 and 2), one kernel.
 cudaError_t launch_assign(km_ctx* c) {
   cudaError_t e;
+  if (c->path == 3) {
+    GemmArgs g{};
+    g.xb = c->xb; g.xa = c->xa_pt; g.xaos = c->xaos; g.cb = c->cbf; g.nprime = c->nprime; g.ctil = c->ctil;
+    g.mu = c->mu; g.shift = c->shift; g.gc = c->gc; g.ls = c->ls; g.labels = c->labels;
+    g.n = c->n; g.k = c->k; g.kpad = c->kpad; g.ntiles = (int)((c->n + 127) / 128);
+    return launch_gemm_assign(c->G, c->st, g);
+  }
   if (c->fast) {
     FastArgs a{};
     a.x = c->x; a.ld = c->ld; a.n = c->n; a.k = c->k; a.kpad = c->kpad;
@@ -120,11 +170,21 @@ cudaError_t launch_assign(km_ctx* c) {
   return e;
 }
 
-// One step: assign + accumulate, then reduce + divide + error + next tables.
+// Mean calculation, error and next tables.
+cudaError_t launch_update_all(km_ctx* c) {
+  if (c->path == 3) {
+    cudaError_t e = launch_msort_step(msort_args(c), c->st);
+    if (e != cudaSuccess) return e;
+    return launch_gemm_prepare(c->st, gemm_prep_args(c));
+  }
+  return launch_update(c->st, update_args(c));
+}
+
+// One step: assign (+ accumulate), then reduce + divide + error + next tables.
 cudaError_t launch_step(km_ctx* c) {
   cudaError_t e = launch_assign(c);
   if (e != cudaSuccess) return e;
-  return launch_update(c->st, update_args(c));
+  return launch_update_all(c);
 }
 
 km_status write_control(km_ctx* c, int done, int max_iter_abs, double tol) {
@@ -194,12 +254,18 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
   }
   c->kpad = (k + 3) / 4 * 4;  // the screen works on groups of 4 centroids
   c->fast = d <= kMaxDFast && k <= kMaxKFast;
+  const bool gemm = d == kGemmD && k <= kGemmMaxK && n < (int64_t(1) << 31) &&
+                    gemm_smem_bytes((k + 255) / 256 * 256) <= (size_t)p.sharedMemPerBlockOptin;
   if (c->fast) {
     c->fast_smem = fast_smem_bytes(d, c->kpad, k);
     if (c->fast_smem > (size_t)p.sharedMemPerBlockOptin) c->fast = false;
   }
   const int64_t ntiles = (n + kWarpTile - 1) / kWarpTile;  // warp-tiles of 256 points
-  if (c->fast) {
+  c->path = c->fast ? 1 : (gemm ? 3 : 2);
+  if (c->path == 3) {
+    c->kpad = (k + 255) / 256 * 256;
+    c->G = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, c->sms));
+  } else if (c->fast) {
     // one resident wave; each warp strides over warp-tiles, and no block
     // takes more than 2^19 points (int64 per-block sums stay in range)
     const int bpsm = fast_blocks_per_sm(d, c->fast_smem);
@@ -230,6 +296,23 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
   KM_CUDA(c, dalloc(&c->ls, 1));
   KM_CUDA(c, dalloc(&c->scan, (size_t)2 * d + 1));
   KM_CUDA(c, dalloc(&c->scan_bad, 1));
+  if (c->path == 3) {
+    KM_CUDA(c, dalloc(reinterpret_cast<uint16_t**>(&c->xb), (size_t)n * kGemmD));
+    KM_CUDA(c, dalloc(&c->xa_pt, (size_t)n));
+    KM_CUDA(c, dalloc(&c->xaos, (size_t)n * kGemmD));
+    KM_CUDA(c, dalloc(reinterpret_cast<uint16_t**>(&c->cbf), (size_t)c->kpad * kGemmD));
+    KM_CUDA(c, dalloc(&c->nprime, (size_t)c->kpad));
+    KM_CUDA(c, dalloc(&c->gc, 1));
+    c->ms_max_chunks = (int)msort_max_chunks(n, k);
+    KM_CUDA(c, dalloc(&c->ms_counts, (size_t)k));
+    KM_CUDA(c, dalloc(&c->ms_offsets, (size_t)k));
+    KM_CUDA(c, dalloc(&c->ms_cfirst, (size_t)k));
+    KM_CUDA(c, dalloc(&c->ms_cursor, (size_t)k));
+    KM_CUDA(c, dalloc(&c->ms_chunks, (size_t)c->ms_max_chunks));
+    KM_CUDA(c, dalloc(&c->ms_nchunks, 1));
+    KM_CUDA(c, dalloc(&c->ms_chunk_sums, (size_t)c->ms_max_chunks * d));
+    KM_CUDA(c, dalloc(&c->ms_perm, (size_t)n));
+  }
   KM_CUDA(c, cudaMemsetAsync(c->ls, 0, sizeof(LoopState), c->st));
   KM_CUDA(c, cudaMemsetAsync(c->counts, 0, sizeof(long long) * k, c->st));
   KM_CUDA(c, cudaMemsetAsync(c->labels, 0, sizeof(int32_t) * n, c->st));
@@ -324,9 +407,13 @@ km_status km_set_points(km_ctx* c, const float* x, int64_t ld, int32_t layout, i
   c->G0 = hdc.G0;
   KM_CUDA(c, cudaMemcpyAsync(c->dc, &hdc, sizeof(hdc), cudaMemcpyHostToDevice, c->st));
   KM_CUDA(c, cudaStreamSynchronize(c->st));
+  if (c->path == 3) {
+    KM_CUDA(c, launch_gemm_prep_points(c->x, c->ld, n, c->shift, c->xb, c->xa_pt, c->xaos, c->st));
+    KM_CUDA(c, cudaStreamSynchronize(c->st));
+  }
   c->have_points = true;
   if (c->have_init) {  // tables depend on the shift and A_max
-    KM_CUDA(c, launch_prepare(c->st, update_args(c)));
+    KM_CUDA(c, launch_tables(c));
     KM_CUDA(c, cudaStreamSynchronize(c->st));
   }
   return KM_OK;
@@ -341,7 +428,7 @@ km_status km_set_init(km_ctx* c, const double* mu0) {
   KM_CUDA(c, cudaMemcpyAsync(c->mu, mu0, sizeof(double) * kd, cudaMemcpyHostToDevice, c->st));
   KM_CUDA(c, cudaMemsetAsync(c->ls, 0, sizeof(LoopState), c->st));
   c->have_init = true;
-  if (c->have_points) KM_CUDA(c, launch_prepare(c->st, update_args(c)));
+  if (c->have_points) KM_CUDA(c, launch_tables(c));
   KM_CUDA(c, cudaStreamSynchronize(c->st));
   std::memset(&c->host_ls, 0, sizeof(c->host_ls));
   return KM_OK;
@@ -428,7 +515,7 @@ km_status km_assign_async(km_ctx* c) {
 km_status km_update_async(km_ctx* c) {
   km_status s = ready(c);
   if (s != KM_OK) return s;
-  KM_CUDA(c, launch_update(c->st, update_args(c)));
+  KM_CUDA(c, launch_update_all(c));
   return KM_OK;
 }
 
@@ -482,7 +569,8 @@ km_status km_get_stats(km_ctx* c, km_stats* out) {
   out->flagged = (int64_t)c->host_ls.last_flagged;
   out->fp64_decided = (int64_t)c->host_ls.last_fp64;
   out->empty_clusters = c->host_ls.empty;
-  out->path = c->fast ? 1 : 2;
+  out->overflowed = (int64_t)c->host_ls.last_overflowed;
+  out->path = c->path;
   return KM_OK;
 }
 

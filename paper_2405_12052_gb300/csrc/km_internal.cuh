@@ -89,6 +89,8 @@ struct LoopState {
   unsigned long long fp64_decided;  // accumulating during a step
   unsigned long long last_flagged;  // of the last completed step
   unsigned long long last_fp64;
+  unsigned long long overflowed;    // tensor-core path: candidate lists that overflowed (this step)
+  unsigned long long last_overflowed;
   unsigned int ticket;              // last-block counter of the reduction
   int32_t error;                    // sticky device error word (0 = none)
 };
@@ -125,6 +127,67 @@ struct GenericArgs {
   const float* B_max_ptr;          // max_k ||c~_k||^2, written by the update kernel
   float tau;
 };
+
+// ---- tensor-core path (d = 64) and sorted mean calculation ----
+constexpr int kGemmD = 64;          // dimension of the tcgen05 path (one 128-byte BF16 row)
+constexpr int kGemmMaxK = 1024;     // centroid rows resident in shared memory
+constexpr int kChunk = 2048;        // points per chunk of the sorted mean calculation
+
+struct GemmConst {
+  float scale;   // -2^(sigma+1)
+  float M;       // 1.5: r = M + 2^sigma (h - 2 S) lies in [1, 2)
+  float c0, c1, cA;  // candidate window Delta(x) = c0 + ||x~|| c1 + ||x~||^2 cA (units of r)
+  float cest;    // extra window of the start estimate per unit ||x~||
+  float B_max;   // max_k ||mu_k - s||^2 (rounded up)
+  float tau;     // tie_rel * (1 + 1e-4)
+  float pad0, pad1;
+};
+
+struct GemmArgs {
+  const void* xb;        // [N][64] BF16 rows of fl(x - s)  (__nv_bfloat16)
+  const float* xa;       // [N] ||fl(x - s)||^2, rounded up
+  const float* xaos;     // [N][64] FP32 points
+  const void* cb;        // [kpad][64] BF16 rows of fl(mu - s)
+  const float* nprime;   // [kpad] n'_k = fl(M + 2^sigma ||mu_k - s||^2)
+  const float* ctil;     // [k][64] fl32(mu - s)
+  const double* mu;      // [k][64]
+  const float* shift;    // [64]
+  const GemmConst* gc;
+  LoopState* ls;
+  int32_t* labels;       // in: previous labels (start estimate); out: labels
+  int64_t n;
+  int k, kpad, ntiles;
+};
+
+struct GemmPrepArgs {
+  const double* mu; const float* shift; int k, kpad;
+  void* cb; float* nprime; float* ctil; GemmConst* gc;
+  float A_max; double tie_rel;
+  const LoopState* ls;
+};
+
+struct MsortArgs {
+  const int32_t* labels; int64_t n; int k; int d;
+  const float* xa;                 // [N][d] FP32 points
+  const DataConst* dc;
+  unsigned long long* counts_u;    // [k]
+  int64_t* offsets;                // [k]
+  int* cfirst;                     // [k] first chunk of each cluster
+  unsigned long long* cursor;      // [k]
+  int4* chunks; int* nchunks; int max_chunks;
+  long long* chunk_sums;           // [max_chunks][d]
+  int32_t* perm;                   // [N]
+  double* mu; long long* counts;   // out
+  LoopState* ls;
+};
+
+cudaError_t launch_gemm_assign(int grid, cudaStream_t st, const GemmArgs& a);
+cudaError_t launch_gemm_prep_points(const float* x, int64_t ld, int64_t n, const float* shift, void* xb, float* xa,
+                                    float* xaos, cudaStream_t st);
+cudaError_t launch_gemm_prepare(cudaStream_t st, const GemmPrepArgs& a);
+size_t gemm_smem_bytes(int kpad);
+int64_t msort_max_chunks(int64_t n, int k);
+cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st);
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_assign_fast(int d, int grid, size_t smem, cudaStream_t st, const FastArgs& a);

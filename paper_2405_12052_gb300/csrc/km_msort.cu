@@ -1,0 +1,233 @@
+// Mean calculation from labels by sorting (paper, section "The Lloyd's
+// algorithm", step 3: mu_k = sum_i 1(z_i = k) x_i / sum_i 1(z_i = k)), for
+// shapes whose per-cluster sums do not fit in shared memory (d > 4 or large
+// K).  Points are grouped by label with a counting sort (histogram, scan,
+// scatter of point indices), each cluster's list is cut into chunks of at
+// most kChunk points, every chunk is summed exactly in fixed point by one
+// block reading whole rows of the N x d copy of the points (coalesced), and
+// the finalize kernel adds each cluster's chunk sums in order in int128,
+// divides, keeps empty centres and forms E^2 by a fixed-order tree.  The
+// scatter order inside a cluster is not deterministic, but integer sums do
+// not depend on it.
+#include "km_internal.cuh"
+
+namespace km {
+
+namespace {
+
+__global__ void ms_hist_kernel(const int32_t* __restrict__ labels, int64_t n, int k,
+                               unsigned long long* counts) {
+  extern __shared__ unsigned int sh[];
+  const bool use_sh = k <= 8192;
+  if (use_sh)
+    for (int c = threadIdx.x; c < k; c += blockDim.x) sh[c] = 0u;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int z = labels[i];
+    if (use_sh) atomicAdd(&sh[z], 1u);
+    else atomicAdd(&counts[z], 1ull);
+  }
+  __syncthreads();
+  if (use_sh)
+    for (int c = threadIdx.x; c < k; c += blockDim.x)
+      if (sh[c]) atomicAdd(&counts[c], (unsigned long long)sh[c]);
+}
+
+// One block: exclusive scans of the counts (point offsets) and of the
+// per-cluster chunk counts; chunk table entries (cluster, start, length).
+__global__ void ms_scan_kernel(const unsigned long long* counts, int k, int64_t* offsets, int* cfirst,
+                               unsigned long long* cursor, int4* chunks, int* nchunks, int max_chunks) {
+  __shared__ long long s_pt[1024];
+  __shared__ int s_ch[1024];
+  __shared__ long long carry_pt;
+  __shared__ int carry_ch;
+  if (threadIdx.x == 0) { carry_pt = 0; carry_ch = 0; }
+  __syncthreads();
+  for (int base = 0; base < k; base += 1024) {
+    const int c = base + threadIdx.x;
+    const long long cnt = c < k ? (long long)counts[c] : 0;
+    const int nch = (int)((cnt + kChunk - 1) / kChunk);
+    s_pt[threadIdx.x] = cnt;
+    s_ch[threadIdx.x] = nch;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scans
+      const long long vp = threadIdx.x >= off ? s_pt[threadIdx.x - off] : 0;
+      const int vc = threadIdx.x >= off ? s_ch[threadIdx.x - off] : 0;
+      __syncthreads();
+      s_pt[threadIdx.x] += vp;
+      s_ch[threadIdx.x] += vc;
+      __syncthreads();
+    }
+    if (c < k) {
+      const long long start = carry_pt + s_pt[threadIdx.x] - cnt;
+      const int cstart = carry_ch + s_ch[threadIdx.x] - nch;
+      offsets[c] = start;
+      cfirst[c] = cstart;
+      cursor[c] = 0ull;
+      for (int q = 0; q < nch && cstart + q < max_chunks; ++q) {
+        const long long a = (long long)q * kChunk;
+        chunks[cstart + q] = make_int4(c, (int)(start + a), (int)min((long long)kChunk, cnt - a), 0);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) { carry_pt += s_pt[1023]; carry_ch += s_ch[1023]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *nchunks = min(carry_ch, max_chunks);
+}
+
+__global__ void ms_scatter_kernel(const int32_t* __restrict__ labels, int64_t n, const int64_t* offsets,
+                                  unsigned long long* cursor, int32_t* perm) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int z = labels[i];
+    const unsigned long long pos = atomicAdd(&cursor[z], 1ull);
+    perm[offsets[z] + (int64_t)pos] = (int32_t)i;
+  }
+}
+
+// One block per chunk: threads (r, j) = (threadIdx.x / d, threadIdx.x % d)
+// sum coordinate j of points r, r + R, ... of the chunk in int64 fixed point
+// (<= kChunk points of |x| < 2^43 grid units each: no overflow); rows are
+// added in order r = 0..R-1.
+__global__ void ms_chunk_sum_kernel(const float* __restrict__ xa, int d, const int32_t* __restrict__ perm,
+                                    const int4* __restrict__ chunks, const int* nchunks, const DataConst* dcp,
+                                    long long* chunk_sums /* [max_chunks][d] */) {
+  extern __shared__ long long s_part[];  // [R][d]
+  const int ch = blockIdx.x;
+  if (ch >= *nchunks) return;
+  const int4 cd = chunks[ch];
+  const int R = blockDim.x / d;
+  const int r = threadIdx.x / d, j = threadIdx.x - r * d;
+  const DataConst dc = *dcp;
+  long long acc = 0;
+  if (r < R) {
+    for (int p = r; p < cd.z; p += R) {
+      const int i = perm[cd.y + p];
+      const float v = xa[(int64_t)i * d + j];
+      const float t = __fadd_rn(v, dc.C_hi);
+      const float h = __fsub_rn(t, dc.C_hi);
+      const float rr = __fsub_rn(v, h);
+      const float t2 = __fadd_rn(rr, dc.C_lo);
+      const long long hi = (long long)(int)(__float_as_uint(t) - dc.bits_C_hi);
+      const long long lo = (long long)(int)(__float_as_uint(t2) - dc.bits_C_lo);
+      acc += (hi << 22) + lo;
+    }
+    s_part[r * d + j] = acc;
+  }
+  __syncthreads();
+  for (int jj = threadIdx.x; jj < d; jj += blockDim.x) {
+    long long s = 0;
+    for (int q = 0; q < R; ++q) s += s_part[q * d + jj];
+    chunk_sums[(size_t)ch * d + jj] = s;
+  }
+}
+
+__device__ __forceinline__ double ms_i128_to_double(unsigned long long lo, long long hs) {
+  unsigned long long hi = (unsigned long long)hs;
+  const bool neg = hs < 0;
+  if (neg) {
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  double r;
+  if (hi == 0ull) {
+    r = __ull2double_rn(lo);
+  } else {
+    const int sh = 64 - __clzll((long long)hi);
+    unsigned long long top = (hi << (64 - sh)) | (lo >> sh);
+    if (lo << (64 - sh)) top |= 1ull;
+    r = ldexp(__ull2double_rn(top), sh);
+  }
+  return neg ? -r : r;
+}
+
+// One block: per (cluster, coordinate), the cluster's chunk sums added in
+// chunk order in int128, one conversion, the divide; E^2 by a fixed-order
+// tree; the stop test.  Centroid tables for the next step are written by the
+// path's own prepare kernel afterwards.
+__global__ void __launch_bounds__(1024) ms_finalize_kernel(const unsigned long long* counts, const int* cfirst,
+                                                           const long long* chunk_sums, int k, int d,
+                                                           const DataConst* dcp, double* mu, long long* counts_out,
+                                                           LoopState* ls) {
+  __shared__ double s_red[1024];
+  __shared__ int s_empty;
+  if (ls->done) return;  // the loop already stopped (graph-driven runs)
+  const int tid = threadIdx.x;
+  if (tid == 0) s_empty = 0;
+  __syncthreads();
+  const int G0 = dcp->G0;
+  double e2p = 0.0;
+  int empty = 0;
+  for (int q = tid; q < k * d; q += blockDim.x) {
+    const int c = q / d, j = q - c * d;
+    const long long cnt = (long long)counts[c];
+    const long long first = cfirst[c];  // index of the cluster's first chunk (from the scan)
+    const int nch = (int)((cnt + kChunk - 1) / kChunk);
+    unsigned long long lo = 0ull;
+    long long hi = 0ll;
+    for (int t = 0; t < nch; ++t) {
+      const long long v = chunk_sums[(size_t)(first + t) * d + j];
+      const unsigned long long nl = lo + (unsigned long long)v;
+      hi += (v < 0 ? -1ll : 0ll) + (nl < lo ? 1ll : 0ll);
+      lo = nl;
+    }
+    const double old = mu[q];
+    double nw = old;
+    if (cnt > 0) nw = __ddiv_rn(ldexp(ms_i128_to_double(lo, hi), G0), (double)cnt);
+    const double df = __dsub_rn(nw, old);
+    e2p = __dadd_rn(e2p, __dmul_rn(df, df));
+    mu[q] = nw;
+    if (j == 0) {
+      counts_out[c] = cnt;
+      empty += cnt == 0;
+    }
+  }
+  s_red[tid] = e2p;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w) s_red[tid] = __dadd_rn(s_red[tid], s_red[tid + w]);
+    __syncthreads();
+  }
+  if (empty) atomicAdd(&s_empty, empty);
+  __syncthreads();
+  if (tid == 0) {
+    const double E2 = s_red[0], E = sqrt(E2);
+    ls->E2 = E2;
+    ls->E = E;
+    ls->iter += 1;
+    ls->empty = s_empty;
+    const double esel = ls->e_mode == 1 ? E2 : E;
+    if (esel < ls->tol) { ls->converged = 1; ls->done = 1; }
+    if (ls->iter >= ls->max_iter) ls->done = 1;
+    ls->last_flagged = ls->flagged;
+    ls->last_fp64 = ls->fp64_decided;
+    ls->last_overflowed = ls->overflowed;
+    ls->flagged = 0ull;
+    ls->fp64_decided = 0ull;
+    ls->overflowed = 0ull;
+  }
+}
+
+}  // namespace
+
+int64_t msort_max_chunks(int64_t n, int k) { return n / kChunk + k + 1; }
+
+cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st) {
+  // callers skip the whole step once the loop has stopped: the flag is read
+  // by the finalize kernel only, so the earlier kernels run unconditionally
+  cudaError_t e = cudaMemsetAsync(a.counts_u, 0, sizeof(unsigned long long) * a.k, st);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, 2048));
+  const size_t hs = a.k <= 8192 ? sizeof(unsigned int) * a.k : 0;
+  ms_hist_kernel<<<(unsigned)blocks, 256, hs, st>>>(a.labels, a.n, a.k, a.counts_u);
+  ms_scan_kernel<<<1, 1024, 0, st>>>(a.counts_u, a.k, a.offsets, a.cfirst, a.cursor, a.chunks, a.nchunks, a.max_chunks);
+  ms_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.labels, a.n, a.offsets, a.cursor, a.perm);
+  const int R = std::max(1, 256 / a.d);
+  const int threads = R * a.d <= 1024 ? R * a.d : a.d;
+  ms_chunk_sum_kernel<<<(unsigned)a.max_chunks, threads, sizeof(long long) * (size_t)std::max(1, threads / a.d) * a.d, st>>>(
+      a.xa, a.d, a.perm, a.chunks, a.nchunks, a.dc, a.chunk_sums);
+  ms_finalize_kernel<<<1, 1024, 0, st>>>(a.counts_u, a.cfirst, a.chunk_sums, a.k, a.d, a.dc, a.mu, a.counts, a.ls);
+  return cudaGetLastError();
+}
+
+}  // namespace km

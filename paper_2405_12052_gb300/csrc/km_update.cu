@@ -256,8 +256,10 @@ __global__ void __launch_bounds__(kRedCols * kRedRows) reduce_update_kernel(Upda
     if (ls->iter >= ls->max_iter) ls->done = 1;
     ls->last_flagged = ls->flagged;
     ls->last_fp64 = ls->fp64_decided;
+    ls->last_overflowed = ls->overflowed;
     ls->flagged = 0ull;
     ls->fp64_decided = 0ull;
+    ls->overflowed = 0ull;
     ls->ticket = 0u;
   }
   __syncthreads();

@@ -1,0 +1,88 @@
+"""GPU parity of the tensor-core (tcgen05 BF16) GEMM-form path, d = 64.
+
+Labels and counts must equal the FP64 oracle's exactly (the BF16 screen only
+proposes candidates; every decision is exact), centroids within 1e-6
+relative, E within 1e-9 absolute.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from test_gpu_parity import assert_centroids_close, lockstep, E_ABS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def km():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2405_12052_gb300 as m
+    m.build()
+    return m
+
+
+@pytest.mark.parametrize("n,k", [(20_000, 64), (20_000, 300), (5_003, 1024), (129, 7), (1_000, 1), (4_096, 257)])
+def test_gemm_lockstep(km, oracle, n, k):
+    x, _, _ = synth.iso_mixture(n, 64, 40, sigma=1.0, box=10.0, seed=n + k)
+    mu0, _ = synth.init_distinct(x, k, seed=k)
+    st = lockstep(km, oracle, x, mu0, steps=2)
+    assert st["path"] == 3
+
+
+def test_gemm_split_clusters_are_resolved_exactly(km, oracle):
+    # twice as many centroids as Gaussians: many points have two near-equal
+    # nearest centres, far inside the BF16 error window
+    x, comp, means = synth.iso_mixture(30_000, 64, 16, sigma=1.0, box=10.0, seed=7)
+    mu0 = np.concatenate([means, means + 0.05]).astype(np.float64)
+    st = lockstep(km, oracle, x, mu0, steps=3)
+    assert st["path"] == 3 and st["flagged"] > 0
+
+
+def test_gemm_full_run(km, oracle):
+    x, _, _ = synth.iso_mixture(40_000, 64, 50, sigma=1.0, box=10.0, seed=3, weights="dirichlet")
+    mu0, _ = synth.init_distinct(x, 50, seed=4)
+    ref = oracle.run(x, mu0, 60, 1e-6)
+    g = km.KMeans(x.shape[1], 64, 50)
+    g.set_points(x)
+    g.set_init(mu0)
+    r = g.run(60, 1e-6)
+    assert r["iters"] == ref["iters"] and r["converged"] == ref["converged"]
+    assert np.array_equal(r["labels"], ref["labels"])
+    assert np.array_equal(g.counts(), ref["counts"])
+    assert_centroids_close(r["centroids"], ref["centroids"], x)
+    assert abs(r["E"] - ref["E"]) <= E_ABS
+    g.close()
+
+
+@pytest.mark.slow
+def test_gemm_full_scale_sampled(km, oracle):
+    """N = 1e7, d = 64, K = 1024 at full size: labels of a 20,000-point sample
+    equal the oracle's argmin; counts are the label histogram; every centroid
+    is the mean of its points (computed here in float64 from the labels)."""
+    w = synth.workload("precision_highd_64d_n1e7_k1024")
+    x, mu0 = w["x"], w["mu0"]
+    n = x.shape[1]
+    g = km.KMeans(n, 64, 1024)
+    g.set_points(x)
+    g.set_init(mu0)
+    g.step()
+    z = g.labels()
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(n, 20_000, replace=False))
+    zs = oracle.assign(np.ascontiguousarray(x[:, sel]), mu0)
+    assert np.array_equal(z[sel], zs)
+    cnt = g.counts()
+    assert np.array_equal(cnt, np.bincount(z, minlength=1024)) and cnt.sum() == n
+    mu = g.centroids()
+    xd = x.astype(np.float64)
+    sums = np.stack([np.bincount(z, weights=xd[j], minlength=1024) for j in range(64)], axis=1)
+    for c in range(1024):
+        ref = sums[c] / cnt[c] if cnt[c] else mu0[c]
+        assert np.linalg.norm(mu[c] - ref) <= 1e-6 * max(np.linalg.norm(ref), 1.0)
+    st = g.stats()
+    assert st["path"] == 3
+    g.close()
