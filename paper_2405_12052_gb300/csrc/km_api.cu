@@ -55,6 +55,9 @@ struct km_ctx {
   void* cbf = nullptr;
   float* nprime = nullptr;
   GemmConst* gc = nullptr;
+  int32_t* rescue_list = nullptr;
+  int4* tie_list = nullptr;
+  unsigned* rescue_count = nullptr;  // [2]: rescue and near-tie list lengths
   // sorted mean calculation
   unsigned long long* ms_counts = nullptr;
   int64_t* ms_offsets = nullptr;
@@ -101,7 +104,7 @@ void free_all(km_ctx* c) {
                   c->ctil4, c->ctil, c->cnorm, c->shift, c->gen_bmax, c->dc, c->ic, c->ls,
                   c->scan, c->scan_bad, c->xb, c->xa_pt, c->xaos, c->cbf, c->nprime, c->gc,
                   c->ms_counts, c->ms_offsets, c->ms_cfirst, c->ms_cursor, c->ms_chunks, c->ms_nchunks,
-                  c->ms_chunk_sums, c->ms_perm};
+                  c->ms_chunk_sums, c->ms_perm, c->rescue_list, c->tie_list, c->rescue_count};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -149,6 +152,8 @@ cudaError_t launch_assign(km_ctx* c) {
     GemmArgs g{};
     g.xb = c->xb; g.xa = c->xa_pt; g.xaos = c->xaos; g.cb = c->cbf; g.nprime = c->nprime; g.ctil = c->ctil;
     g.mu = c->mu; g.shift = c->shift; g.gc = c->gc; g.ls = c->ls; g.labels = c->labels;
+    g.rescue_list = c->rescue_list; g.tie_list = c->tie_list;
+    g.rescue_count = c->rescue_count; g.tie_count = c->rescue_count + 1;
     g.n = c->n; g.k = c->k; g.kpad = c->kpad; g.ntiles = (int)((c->n + 127) / 128);
     return launch_gemm_assign(c->G, c->st, g);
   }
@@ -297,12 +302,15 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
   KM_CUDA(c, dalloc(&c->scan, (size_t)2 * d + 1));
   KM_CUDA(c, dalloc(&c->scan_bad, 1));
   if (c->path == 3) {
-    KM_CUDA(c, dalloc(reinterpret_cast<uint16_t**>(&c->xb), (size_t)n * kGemmD));
+    KM_CUDA(c, dalloc(reinterpret_cast<uint16_t**>(&c->xb), (size_t)gemm_xb_rows(n) * kGemmD));
     KM_CUDA(c, dalloc(&c->xa_pt, (size_t)n));
     KM_CUDA(c, dalloc(&c->xaos, (size_t)n * kGemmD));
     KM_CUDA(c, dalloc(reinterpret_cast<uint16_t**>(&c->cbf), (size_t)c->kpad * kGemmD));
     KM_CUDA(c, dalloc(&c->nprime, (size_t)c->kpad));
     KM_CUDA(c, dalloc(&c->gc, 1));
+    KM_CUDA(c, dalloc(&c->rescue_list, (size_t)n));
+    KM_CUDA(c, dalloc(&c->tie_list, (size_t)n * 3));
+    KM_CUDA(c, dalloc(&c->rescue_count, 2));
     c->ms_max_chunks = (int)msort_max_chunks(n, k);
     KM_CUDA(c, dalloc(&c->ms_counts, (size_t)k));
     KM_CUDA(c, dalloc(&c->ms_offsets, (size_t)k));

@@ -3,21 +3,31 @@
 // expectation step of Lloyd's algorithm (paper, section "The Lloyd's
 // algorithm", step 2) where d is large enough for a dense contraction.
 //
-// Per CTA (one per SM, 512 threads): the whole centroid matrix stays in
-// shared memory as BF16 rows of 128 bytes in the 128-byte-swizzled K-major
-// layout; point tiles of 128 rows are double-buffered with cp.async.  One
-// thread issues M=128, N=256, K=16 MMAs into two TMEM accumulators of 256
-// columns (commit -> mbarrier, bounded waits).  16 warps read TMEM (4 per
-// lane quarter, 64 columns each), form r_k = M + 2^sigma (h_k - 2 S_k) in one
-// binade, and keep every centroid whose r is within the candidate window
-// Delta(x) of the point's running minimum (the window bounds every BF16 and
-// FP32 rounding plus 1e-5 * D: it always holds the exact argmin and all
-// near ties).  The running minimum starts from the point's previous label,
-// evaluated on the resident tiles.  A point with one candidate is decided;
-// otherwise its candidates are re-ranked exactly (FP32 direct form with a
-// rigorous bound, then FP64 in the oracle's order), over all K if the
-// candidate list overflows.  Labels only; the sums are formed by the sorted
-// mean calculation.
+// Persistent, warp-specialised CTA (one per SM, 17 warps):
+//  * warp 16, one thread: bulk copies (cp.async.bulk, mbarrier tx counts) of
+//    the whole BF16 centroid matrix once and of 128-point tiles into two
+//    stages, both pre-swizzled in global memory to the 128-byte K-major
+//    layout; and the MMAs: per tile, K/256 groups of M=128, N=256, K=4x16
+//    into two TMEM accumulators of 256 columns (double-buffered against the
+//    epilogue through full/empty mbarriers).
+//  * warps 0-15, the epilogue: warp w reads TMEM lanes 32 (w % 4) (its 32
+//    points) and 64 columns of each group, forms r_k = n'_k + scale S_k (one
+//    binade [1, 2): r = M + 2^sigma (h - 2 S)) and the minimum of each half
+//    of 16 columns.  A half whose minimum is within the point's threshold is
+//    stored whole to shared memory (up to kSlots halves per point, 16 bits
+//    per value relative to the half's minimum).  The threshold is the
+//    best r seen so far plus the candidate window Delta(x), which bounds every
+//    BF16 and FP32 rounding of the screen plus the oracle's FP64 error and
+//    1e-5 D, so the kept set always holds the exact argmin and all near ties.
+//    For the first group the epilogue takes two passes (minima, a barrier,
+//    then the stores), so the threshold already covers 256 centroids.
+//  * resolve, 4 threads per point: the stored values under the final
+//    threshold are the candidates.  One candidate decides the label;
+//    otherwise the candidates are re-ranked by the FP32 direct form with a
+//    rigorous bound, then in FP64 in the oracle's order.  Points whose halves
+//    did not fit go to a list that a second kernel resolves exactly over all
+//    K (a fraction of a percent of points on split clusters).
+// Labels only; the sums are formed by the sorted mean calculation.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -28,11 +38,28 @@ namespace km {
 
 namespace {
 
-constexpr int kGM = 128;        // points per tile = TMEM lanes
-constexpr int kGN = 256;        // centroids per MMA group = TMEM columns per accumulator
-constexpr int kGThreads = 512;  // 16 warps
-constexpr int kGCand = 32;      // candidates kept per point
+constexpr int kGM = 128;          // points per tile = TMEM lanes
+constexpr int kGN = 256;          // centroids per MMA group = TMEM columns per accumulator
+constexpr int kEpiWarps = 16;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kGThreads = kEpiThreads + 32;  // + the producer warp
+constexpr int kSlots = 12;        // stored halves per point
+constexpr int kHalf = 16;         // values per stored half
+constexpr int kPtStride = kSlots * kHalf * 2 + 16;  // bytes per point (padding spreads banks)
+constexpr int kTileBytes = kGM * kGemmD * 2;   // 16 KB of BF16 per point tile
+constexpr int kTieMax = 20;       // candidates per near-tie list entry (48 bytes)
 constexpr long kWaitLimit = 1L << 22;
+// shared-memory layout (bytes from the 1024-aligned base)
+constexpr int kOffStore = 0;                                  // [128][kPtStride] bytes
+constexpr int kOffSk = kOffStore + kGM * kPtStride;           // [128][kSlots] int16
+constexpr int kOffSmin = kOffSk + kGM * kSlots * 2;           // [128][kSlots] u32
+constexpr int kOffThr = kOffSmin + kGM * kSlots * 4;          // [2][128] u32
+constexpr int kOffCnt = kOffThr + 2 * kGM * 4;                // [128] int
+constexpr int kOffOver = kOffCnt + kGM * 4;                   // [128] int
+constexpr int kOffStat = kOffOver + kGM * 4;                  // [4] int
+constexpr int kOffBar = kOffStat + 16;                        // [10] mbarriers
+constexpr int kOffTmem = kOffBar + 10 * 8;                    // TMEM base address
+constexpr int kOffOperands = (kOffTmem + 4 + 1023) / 1024 * 1024;
 
 __device__ __forceinline__ uint64_t sm_desc(uint32_t saddr) {
   // K-major, 128-byte swizzle: start address, LBO 16 B (unused), SBO 1024 B
@@ -52,63 +79,89 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// bulk global -> shared copy completing on an mbarrier (16-byte aligned
+// addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
 __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait on an mbarrier phase (at most ~1 s and kWaitLimit polls);
-// returns false if it gave up.
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
-  uint32_t ok = 0;
-  const uint64_t t0 = gtimer();
-  for (long it = 0; it < kWaitLimit && !ok; ++it) {
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-    if (!ok && (it & 63) == 63 && gtimer() - t0 > 1000000000ull) break;
-  }
+// Bounded wait on an mbarrier phase: each try may suspend the thread for up
+// to 20 us until the phase completes; gives up (returns false) after ~1 s.
+__device__ __forceinline__ bool try_bar(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(bar), "r"(parity), "r"(20000) : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-                 "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                 "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
+  if (try_bar(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (long it = 0; it < kWaitLimit; ++it) {
+    if (try_bar(bar, parity)) return true;
+    if (gtimer() - t0 > 1000000000ull) break;
+  }
+  return false;
+}
+// 32 consecutive TMEM columns of the warp's 32 lanes, waited for, as 16
+// pairs of FP32 values (column 2q in the low half of v[q])
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, unsigned long long* v) {
+  asm volatile("{\n.reg .b32 t0,t1,t2,t3,t4,t5,t6,t7,t8,t9,t10,t11,t12,t13,t14,t15,t16,t17,t18,t19,t20,t21,t22,t23,t24,t25,t26,t27,t28,t29,t30,t31;\n"
+               "tcgen05.ld.sync.aligned.32x32b.x32.b32 {t0,t1,t2,t3,t4,t5,t6,t7,t8,t9,t10,t11,t12,t13,t14,t15,t16,t17,t18,t19,t20,t21,t22,t23,t24,t25,t26,t27,t28,t29,t30,t31}, [%16];\n"
+               "tcgen05.wait::ld.sync.aligned;\n"
+               "mov.b64 %0, {t0, t1};\nmov.b64 %1, {t2, t3};\nmov.b64 %2, {t4, t5};\nmov.b64 %3, {t6, t7};\nmov.b64 %4, {t8, t9};\nmov.b64 %5, {t10, t11};\nmov.b64 %6, {t12, t13};\nmov.b64 %7, {t14, t15};\nmov.b64 %8, {t16, t17};\nmov.b64 %9, {t18, t19};\nmov.b64 %10, {t20, t21};\nmov.b64 %11, {t22, t23};\nmov.b64 %12, {t24, t25};\nmov.b64 %13, {t26, t27};\nmov.b64 %14, {t28, t29};\nmov.b64 %15, {t30, t31};\n}"
+               : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3]), "=l"(v[4]), "=l"(v[5]), "=l"(v[6]), "=l"(v[7]), "=l"(v[8]), "=l"(v[9]), "=l"(v[10]), "=l"(v[11]), "=l"(v[12]), "=l"(v[13]), "=l"(v[14]), "=l"(v[15])
+               : "r"(taddr) : "memory");
 }
 __device__ __forceinline__ float fmin3g(float a, float b, float c) {
   float d;
   asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
   return d;
 }
-__device__ __forceinline__ void cp16(uint32_t dst, const void* src, int bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes));
+// paired FP32 FMA, round to nearest: (a.lo, a.hi) * (b.lo, b.hi) + (c.lo, c.hi)
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
 }
-// byte offset of 16-byte chunk c of row r in a 128B-swizzled K-major tile
-__device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+__device__ __forceinline__ float lo_f(unsigned long long v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi_f(unsigned long long v) { return __uint_as_float((uint32_t)(v >> 32)); }
+// Barrier of the 16 epilogue warps (named barrier 1) that also ORs a flag.
+__device__ __forceinline__ bool epi_sync_or(bool v) {
+  uint32_t r;
+  asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
+               : "=r"(r) : "r"((uint32_t)v), "n"(kEpiThreads) : "memory");
+  return r != 0;
+}
+// BF16 element index of (row, j) in the 128-byte-swizzled K-major layout
+// (16-byte chunk j / 8 of row r sits at chunk (j / 8) ^ (r % 8))
+__host__ __device__ __forceinline__ int64_t swz_index(int64_t row, int j) {
+  return row * kGemmD + ((((j >> 3) ^ (int)(row & 7)) << 3) | (j & 7));
+}
 
 constexpr float kGU = 5.9604644775390625e-08f;  // 2^-24
 
-// FP32 direct form sum_j (x~_j - c~_j)^2 and its bound against the exact D
-// plus the oracle's FP64 rounding (d = 64).
-__device__ __forceinline__ float direct64(const float* __restrict__ xrow, const float* __restrict__ s,
-                                          const float* __restrict__ crow) {
-  float dv = 0.f;
-  for (int j = 0; j < kGemmD; ++j) {
-    const float t = __fsub_rn(__fsub_rn(xrow[j], s[j]), crow[j]);
-    dv = __fmaf_rn(t, t, dv);
-  }
-  return dv;
-}
+// Bound on |FP32 direct form - FP64 oracle distance| (d = 64): the FP32
+// rounding of sum_j (x~_j - c~_j)^2 against the exact D plus the oracle's own
+// FP64 rounding.
 __device__ __forceinline__ float bound64(float dv, float sA, float sB, float AB) {
   const float sd = sqrtf(fmaxf(dv, 0.f));
   return 1.01f * kGU * ((float)(kGemmD + 2) * dv + 2.f * sd * (sA + sB)) + 4.6e-16f * (float)(kGemmD + 1) * AB + 1e-30f;
 }
+// The oracle's distance: FP64, coordinates in order.
 __device__ __forceinline__ double d64row(const float* __restrict__ xrow, const double* __restrict__ mrow) {
   double acc = 0.0;
   for (int j = 0; j < kGemmD; ++j) {
@@ -118,6 +171,38 @@ __device__ __forceinline__ double d64row(const float* __restrict__ xrow, const d
   return acc;
 }
 
+struct EpiSmem {
+  unsigned char* store;  // [128][kPtStride]: per slot 16 values, 16 bits each (below)
+  short* sk;        // [128][kSlots] first centroid of each stored half
+  uint32_t* smin;   // [128][kSlots] float bits of the half's minimum m
+  uint32_t* thr;    // [2][128] shared threshold (float bits), by tile parity
+  int* cnt;         // [128] halves allocated
+  int* over;        // [128] 1 if a half did not fit
+};
+
+// Keep the 16 values v[0..15] (columns k0..k0+15) of point p; past kSlots
+// halves the point goes to the rescue list.  Every r lies in the binade
+// [1, 2), so bits(r) - bits(m) = (r - m) 2^23 exactly; bits 8..23 of it are
+// stored (r - m in units of 2^-15, truncated): m + q 2^-15 <= r, so no value
+// under the final threshold can test above it.
+__device__ __forceinline__ void store_half(const EpiSmem& s, int p, const unsigned long long* u, int k0, float mn) {
+  const int slot = atomicAdd(&s.cnt[p], 1);
+  if (slot < kSlots) {
+    const uint32_t bm = __float_as_uint(mn);
+    uint32_t w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      w[q] = __byte_perm((uint32_t)u[q] - bm, (uint32_t)(u[q] >> 32) - bm, 0x6521);
+    uint4* dst = reinterpret_cast<uint4*>(s.store + p * kPtStride + slot * kHalf * 2);
+    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    s.sk[p * kSlots + slot] = (short)k0;
+    s.smin[p * kSlots + slot] = bm;
+  } else {
+    s.over[p] = 1;
+  }
+}
+
 __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
   extern __shared__ unsigned char raw[];
   if (a.ls->done) return;
@@ -125,99 +210,160 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
   // the shared address space visible to the compiler)
   unsigned char* sm = raw + ((1024u - ((uint32_t)__cvta_generic_to_shared(raw) & 1023u)) & 1023u);
   const int kpad = a.kpad, NT = kpad / kGN;
-  unsigned char* sC = sm;                                // kpad x 128 B
-  unsigned char* sA = sC + (size_t)kpad * 128;           // 2 x 16 KB
-  float* s_np = reinterpret_cast<float*>(sA + 2 * kGM * 128);  // [kpad] n'_k
-  uint32_t* s_thr = reinterpret_cast<uint32_t*>(s_np + kpad);  // [128] float bits
-  int* s_cnt = reinterpret_cast<int*>(s_thr + kGM);            // [128]
-  uint32_t* s_cand = reinterpret_cast<uint32_t*>(s_cnt + kGM); // [128][kGCand]
-  float* s_candr = reinterpret_cast<float*>(s_cand + kGM * kGCand);
-  float* s_delta = s_candr + kGM * kGCand;                     // [128]
-  float* s_shift = s_delta + kGM;                               // [64]
-  int* s_stat = reinterpret_cast<int*>(s_shift + kGemmD);       // [4]
-  unsigned long long* s_bar = reinterpret_cast<unsigned long long*>(s_stat + 4);  // [2], 8-aligned
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + 2);
+  // fixed-offset per-point arrays first, then the 1024-aligned operand tiles
+  EpiSmem es;
+  es.store = sm + kOffStore;
+  es.sk = reinterpret_cast<short*>(sm + kOffSk);
+  es.smin = reinterpret_cast<uint32_t*>(sm + kOffSmin);
+  es.thr = reinterpret_cast<uint32_t*>(sm + kOffThr);
+  es.cnt = reinterpret_cast<int*>(sm + kOffCnt);
+  es.over = reinterpret_cast<int*>(sm + kOffOver);
+  int* s_stat = reinterpret_cast<int*>(sm + kOffStat);                                  // [4]
+  unsigned long long* s_bar = reinterpret_cast<unsigned long long*>(sm + kOffBar);      // [10]
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + kOffTmem);
+  unsigned char* sC = sm + kOffOperands;                        // kpad x 128 B
+  unsigned char* sA = sC + (size_t)kpad * 128;                  // 2 x 16 KB
+  float* s_np = reinterpret_cast<float*>(sA + 2 * kTileBytes);  // [kpad] n'_k
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quarter = warp & 3, cslice = warp >> 2;  // TMEM lanes 32*quarter.., columns 64*cslice..
-  const GemmConst gc = *a.gc;
-  const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&s_bar[0]);
-  const uint32_t bar1 = (uint32_t)__cvta_generic_to_shared(&s_bar[1]);
-
+  auto bar_addr = [&](int q) { return (uint32_t)__cvta_generic_to_shared(&s_bar[q]); };
+  // barriers: 0-1 a_full, 2-3 a_empty, 4-5 acc_full, 6-7 acc_empty, 8 centroids, 9 final
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      (uint32_t)__cvta_generic_to_shared(s_tmem)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1));
+    // a_empty completes on the MMAs' commit and on every epilogue warp
+    // (the start estimate reads the point tile)
+    for (int q = 0; q < 6; ++q) bar_init(bar_addr(q), (q == 2 || q == 3) ? 1 + kEpiWarps : 1);
+    bar_init(bar_addr(6), kEpiWarps);
+    bar_init(bar_addr(7), kEpiWarps);
+    bar_init(bar_addr(8), 1);
+    bar_init(bar_addr(9), 1);
   }
   if (tid < 4) s_stat[tid] = 0;
-  for (int j = tid; j < kGemmD; j += kGThreads) s_shift[j] = a.shift[j];
   for (int c = tid; c < kpad; c += kGThreads) s_np[c] = a.nprime[c];
-  // centroid tiles, resident for the whole kernel
-  for (int u = tid; u < kpad * 8; u += kGThreads) {
-    const int r = u >> 3, c = u & 7;
-    cp16((uint32_t)__cvta_generic_to_shared(sC + swz(r, c)), reinterpret_cast<const __nv_bfloat16*>(a.cb) + (size_t)r * kGemmD + c * 8, 16);
-  }
-  const int ntiles = a.ntiles;
-  auto load_a = [&](int tile, int buf) {
-    unsigned char* dstb = sA + buf * (kGM * 128);
-    for (int u = tid; u < kGM * 8; u += kGThreads) {
-      const int r = u >> 3, c = u & 7;
-      const int64_t row = (int64_t)tile * kGM + r;
-      const bool ok = row < a.n;
-      cp16((uint32_t)__cvta_generic_to_shared(dstb + swz(r, c)), reinterpret_cast<const __nv_bfloat16*>(a.xb) + (ok ? row : 0) * kGemmD + c * 8, ok ? 16 : 0);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  if ((int)blockIdx.x < ntiles) load_a(blockIdx.x, 0);
+  for (int q = tid; q < kGM * kSlots; q += kGThreads) es.smin[q] = 0u;
+  for (int q = tid; q < 2 * kGM; q += kGThreads) es.thr[q] = 0x7f800000u;  // +inf
+  for (int q = tid; q < kGM; q += kGThreads) { es.cnt[q] = 0; es.over[q] = 0; }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *s_tmem;
-  const uint32_t sC_addr = (uint32_t)__cvta_generic_to_shared(sC);
-  uint32_t ph0 = 0, ph1 = 0;  // mbarrier phases
+  const int ntiles = a.ntiles;
+  const int nloc = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const GemmConst gc = *a.gc;
   bool aborted = false;
-  int nflag = 0, n64 = 0, nover = 0;
 
-  int local = 0;
-  for (int tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x, ++local) {
-    const int buf = local & 1;
-    const uint32_t sA_addr = (uint32_t)__cvta_generic_to_shared(sA + buf * (kGM * 128));
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    auto issue = [&](int nt) {  // one thread: group nt into accumulator nt & 1
-      const uint32_t d = tmem + (uint32_t)((nt & 1) * kGN);
-      const uint32_t bbase = sC_addr + (uint32_t)(nt * kGN * 128);
+  if (warp == kEpiWarps) {
+    // ---------------- producer: loads and MMAs (one thread) ----------------
+    if (lane == 0) {
+      const uint32_t sC_addr = (uint32_t)__cvta_generic_to_shared(sC);
+      const uint32_t sA_addr = (uint32_t)__cvta_generic_to_shared(sA);
+      const unsigned char* xb = reinterpret_cast<const unsigned char*>(a.xb);
+      auto load_tile = [&](int l) {
+        const int s = l & 1;
+        const int64_t tile = (int64_t)blockIdx.x + (int64_t)l * gridDim.x;
+        bar_expect_tx(bar_addr(s), kTileBytes);
+        bulk_load(sA_addr + s * kTileBytes, xb + tile * kTileBytes, kTileBytes, bar_addr(s));
+      };
+      int loads = 0;  // tiles whose load was issued
+      if (nloc > 0) {
+        bar_expect_tx(bar_addr(8), (uint32_t)kpad * 128u);
+        bulk_load(sC_addr, a.cb, (uint32_t)kpad * 128u, bar_addr(8));
+        for (; loads < min(2, nloc); ++loads) load_tile(loads);
+        bool ok = wait_bar(bar_addr(8), 0);
+        int gcount = 0, pending = -1;
+        for (int l = 0; l < nloc && ok; ++l) {
+          const int s = l & 1;
+          ok = wait_bar(bar_addr(s), (uint32_t)(l >> 1) & 1u);
+          for (int g = 0; g < NT && ok; ++g, ++gcount) {
+            const int b = gcount & 1;
+            if (gcount >= 2) ok = wait_bar(bar_addr(6 + b), ((uint32_t)(gcount >> 1) & 1u) ^ 1u);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t d = tmem + (uint32_t)(b * kGN);
+            const uint32_t abase = sA_addr + s * kTileBytes, bbase = sC_addr + (uint32_t)(g * kGN * 128);
 #pragma unroll
-      for (int kk = 0; kk < kGemmD / 16; ++kk)
-        mma_bf16(d, sm_desc(sA_addr + kk * 32), sm_desc(bbase + kk * 32), kk > 0 ? 1u : 0u);
-      mma_commit((nt & 1) ? bar1 : bar0);
-    };
-    if (tid == 0) {
-      issue(0);
-      if (NT > 1) issue(1);
+            for (int kk = 0; kk < kGemmD / 16; ++kk)
+              mma_bf16(d, sm_desc(abase + kk * 32), sm_desc(bbase + kk * 32), kk > 0 ? 1u : 0u);
+            mma_commit(bar_addr(4 + b));
+            if (g == 0 && pending >= 0) {
+              // tile pending's MMAs were queued before this group: its stage
+              // frees up while this group runs
+              ok = wait_bar(bar_addr(2 + (pending & 1)), (uint32_t)(pending >> 1) & 1u);
+              if (ok) { load_tile(pending + 2); ++loads; }
+              pending = -1;
+            }
+          }
+          if (!ok) break;
+          mma_commit(bar_addr(2 + s));  // stage s is free once these MMAs complete
+          if (l + 2 < nloc) pending = l;
+        }
+        if (!ok) a.ls->error = 3;  // a wait gave up
+        // every MMA and copy issued must complete before TMEM and shared
+        // memory are released
+        mma_commit(bar_addr(9));
+        wait_bar(bar_addr(9), 0);
+        if (!ok)
+          for (int l = max(0, loads - 2); l < loads; ++l) {
+            // the last copy into each stage may still be in flight (earlier
+            // ones were consumed before their stage was reloaded)
+            wait_bar(bar_addr(l & 1), (uint32_t)(l >> 1) & 1u);
+          }
+      }
     }
-    // per-point start: threshold from the previous label, on the resident tiles
-    if (tid < kGM) {
-      const int p = tid;
-      const int64_t i = (int64_t)tile * kGM + p;
-      uint32_t thr_bits = 0u;  // rows past N keep no candidates
-      if (i < a.n) {
-        int z = a.labels[i];
-        z = (z >= 0 && z < a.k) ? z : 0;
-        const unsigned char* arow = sA + buf * (kGM * 128);
-        float S = 0.f;
-#pragma unroll 1
-        for (int c = 0; c < 8; ++c) {
-          const uint4 xv = *reinterpret_cast<const uint4*>(arow + swz(p, c));
-          const uint4 cv = *reinterpret_cast<const uint4*>(sC + swz(z, c));
+  } else {
+    // ---------------- epilogue warps ----------------
+    const int quarter = warp & 3, cslice = warp >> 2;
+    const int p = quarter * 32 + lane;  // TMEM lane = point within the tile
+    const bool cold = a.ls->iter == 0;  // labels not yet from these centres' predecessors
+    // the centroid matrix is resident (block-uniform decision: the named
+    // barriers below need every epilogue warp)
+    if (nloc > 0) {
+      const bool ok8 = wait_bar(bar_addr(8), 0);
+      __syncwarp();
+      aborted = epi_sync_or(!ok8);
+      if (aborted) a.ls->error = 3;
+    }
+    int gcount = 0;
+    int nflag = 0, nresc = 0;
+    // per-point inputs of the next tile are loaded one tile ahead: z and
+    // ||x~||^2 for the start estimate (4 threads per point, point tid / 4)
+    // and ||x~||^2 for the window (point p)
+    const int pp = tid >> 2, sub = tid & 3;
+    int nz = 0;
+    float nA4 = 0.f, nA = 0.f;
+    auto prefetch = [&](int l) {
+      if (l >= nloc) return;
+      const int64_t t = (int64_t)blockIdx.x + (int64_t)l * gridDim.x;
+      const int64_t i4 = t * kGM + pp, i1 = t * kGM + p;
+      nz = i4 < a.n ? a.labels[i4] : 0;
+      nA4 = i4 < a.n ? a.xa[i4] : 0.f;
+      nA = i1 < a.n ? a.xa[i1] : 0.f;
+    };
+    // Start threshold of tile l from each point's previous label z (any
+    // label in range bounds the minimum): r_z from the resident BF16
+    // operands, 4 threads per point with 16 coordinates each, plus the window
+    // and a bound on its difference from the tensor-core value of r_z.
+    // Computed before the barrier that ends the previous tile, which
+    // publishes it to the other warps.
+    auto start_estimate = [&](int l, int z, float A4) {
+      const int s = l & 1;
+      const int64_t tile = (int64_t)blockIdx.x + (int64_t)l * gridDim.x;
+      const bool okp = __all_sync(0xffffffffu, wait_bar(bar_addr(s), (uint32_t)(l >> 1) & 1u));
+      const int64_t ii = tile * kGM + pp;
+      float S = 0.f;
+      z = (z >= 0 && z < a.k) ? z : 0;
+      if (okp && ii < a.n) {
+        const unsigned char* xr = sA + s * kTileBytes;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = 2 * sub + h;  // 16-byte chunk: coordinates 8c .. 8c+7
+          const uint4 xv = *reinterpret_cast<const uint4*>(xr + pp * 128 + ((c ^ (pp & 7)) << 4));
+          const uint4 cv = *reinterpret_cast<const uint4*>(sC + (size_t)z * 128 + ((c ^ (z & 7)) << 4));
           const __nv_bfloat162* xh = reinterpret_cast<const __nv_bfloat162*>(&xv);
           const __nv_bfloat162* ch = reinterpret_cast<const __nv_bfloat162*>(&cv);
 #pragma unroll
@@ -227,219 +373,373 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
             S = __fmaf_rn(xf.y, cf.y, S);
           }
         }
-        const float A = a.xa[i];
-        const float nx = sqrtf(A);
-        const float delta = gc.c0 + nx * gc.c1 + A * gc.cA;
-        s_delta[p] = delta;
-        const float r_est = __fmaf_rn(S, gc.scale, s_np[z]);
-        thr_bits = __float_as_uint(r_est + delta + nx * gc.cest);
       }
-      s_thr[p] = thr_bits;
-      s_cnt[p] = 0;
-    }
-    // prefetch the next tile's points into the other buffer (its last MMAs
-    // completed in the previous tile)
-    if (tile + (int)gridDim.x < ntiles) load_a(tile + gridDim.x, buf ^ 1);
-    __syncthreads();
-
-    const int p = quarter * 32 + lane;  // this thread's point (TMEM lane)
-    // Two accumulators are read per round: first their chunk minima tighten
-    // the point's threshold (over up to 512 centroids), then the chunks whose
-    // minimum passes it are read again and their candidates collected.
-    for (int nt0 = 0; nt0 < NT; nt0 += 2) {
-      const int ng = min(2, NT - nt0);
-      bool ok = true;
-      for (int g = 0; g < ng; ++g) {
-        const int nt = nt0 + g;
-        ok = wait_bar((nt & 1) ? bar1 : bar0, (nt & 1) ? ph1 : ph0) && ok;
-        if (nt & 1) ph1 ^= 1u; else ph0 ^= 1u;
+      S = __fadd_rn(S, __shfl_xor_sync(0xffffffffu, S, 1));
+      S = __fadd_rn(S, __shfl_xor_sync(0xffffffffu, S, 2));
+      if (okp && ii < a.n && sub == 0) {
+        const float nx = sqrtf(A4);
+        const float t0 = __fmaf_rn(S, gc.scale, s_np[z]) + (gc.c0 + 4.8e-7f) + nx * (gc.c1 + gc.cest) + A4 * gc.cA;
+        atomicMin(&es.thr[(l & 1) * kGM + pp], __float_as_uint(t0));
       }
-      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below needs the whole warp
-      if (!ok) a.ls->error = 3;          // an MMA group did not complete in time
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const float delta = s_delta[p];
-      float mins[2][2];
-      if (ok) {
+      __syncwarp();
+      if (lane == 0) bar_arrive(bar_addr(2 + s));  // done with the point tile
+      if (!okp) a.ls->error = 3;
+    };
+    const unsigned long long sc2 = ((unsigned long long)__float_as_uint(gc.scale) << 32) | __float_as_uint(gc.scale);
+    prefetch(0);
+    if (nloc > 0 && !aborted) start_estimate(0, nz, nA4);
+    float curA = nA;
+    prefetch(1);
+    __syncwarp();
+    aborted = epi_sync_or(aborted);
+    for (int l = 0; l < nloc && !aborted; ++l) {
+      const int par = l & 1;
+      const int64_t tile = (int64_t)blockIdx.x + (int64_t)l * gridDim.x;
+      const int64_t i = tile * kGM + p;
+      const bool valid = i < a.n;
+      const float A = curA;
+      const float delta = gc.c0 + sqrtf(A) * gc.c1 + A * gc.cA;
+      uint32_t* thr_sh = es.thr + par * kGM;
+      float thr = __uint_as_float(0x7f800000u);
+      for (int g = 0; g < NT; ++g, ++gcount) {
+        const int b = gcount & 1;
+        bool ok = wait_bar(bar_addr(4 + b), (uint32_t)(gcount >> 1) & 1u);
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below needs the whole warp
+        if (!ok) a.ls->error = 3;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kGN + cslice * 64);
+        const int kb = g * kGN + cslice * 64;
+        // 32 columns: r values (16 pairs) and the minima of their two halves
+        auto chunk = [&](int h2, unsigned long long* u, float& m0, float& m1) {
+          tmem_ld32(ta + 32 * h2, u);
 #pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          if (g < ng) {
-            const int nt = nt0 + g;
+          for (int q = 0; q < 16; q += 2) {
+            const ulonglong2 np = *reinterpret_cast<const ulonglong2*>(s_np + kb + 32 * h2 + 2 * q);
+            u[q] = fma2(u[q], sc2, np.x);
+            u[q + 1] = fma2(u[q + 1], sc2, np.y);
+          }
+          float x0 = fmin3g(lo_f(u[0]), hi_f(u[0]), lo_f(u[1])), x1 = fmin3g(lo_f(u[8]), hi_f(u[8]), lo_f(u[9]));
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int col = cslice * 64 + h * 32;
-              float v[32];
-              tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((nt & 1) * kGN + col), v);
-              const int k0 = nt * kGN + col;
+          for (int q = 1; q < 7; ++q) {
+            x0 = fmin3g(x0, hi_f(u[q]), lo_f(u[q + 1]));
+            x1 = fmin3g(x1, hi_f(u[8 + q]), lo_f(u[9 + q]));
+          }
+          m0 = fminf(x0, hi_f(u[7]));
+          m1 = fminf(x1, hi_f(u[15]));
+        };
+        auto keep = [&](const unsigned long long* u, int kc, float m) {
+          if (m <= thr) store_half(es, p, u, kc, m);
+          thr = fminf(thr, m + delta);
+        };
+        auto release = [&]() {  // the accumulator may be overwritten
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) bar_arrive(bar_addr(6 + b));
+        };
+        if (g == 0 && cold) {
+          // first step after new centres (the labels give no start
+          // threshold): minima of the first 256 columns first, then the
+          // halves within the threshold are read again and stored
+          float mn[4] = {0.f, 0.f, 0.f, 0.f};
+          if (ok) {
+            unsigned long long v[16];
+            chunk(0, v, mn[0], mn[1]);
+            chunk(1, v, mn[2], mn[3]);
+            if (valid) atomicMin(&thr_sh[p], __float_as_uint(fminf(fminf(mn[0], mn[1]), fminf(mn[2], mn[3])) + delta));
+          }
+          __syncwarp();
+          aborted = epi_sync_or(!ok);
+          if (aborted) break;
+          thr = __uint_as_float(thr_sh[p]);
 #pragma unroll
-              for (int q = 0; q < 32; q += 4) {
-                const float4 np = *reinterpret_cast<const float4*>(s_np + k0 + q);
-                v[q] = __fmaf_rn(v[q], gc.scale, np.x);
-                v[q + 1] = __fmaf_rn(v[q + 1], gc.scale, np.y);
-                v[q + 2] = __fmaf_rn(v[q + 2], gc.scale, np.z);
-                v[q + 3] = __fmaf_rn(v[q + 3], gc.scale, np.w);
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const bool need = valid && (mn[2 * h2] <= thr || mn[2 * h2 + 1] <= thr);
+            if (__any_sync(0xffffffffu, need)) {
+              unsigned long long v[16];
+              float m0, m1;
+              chunk(h2, v, m0, m1);
+              if (valid) {
+                keep(v, kb + 32 * h2, mn[2 * h2]);
+                keep(v + 8, kb + 32 * h2 + 16, mn[2 * h2 + 1]);
               }
-              float mn = fmin3g(v[0], v[1], v[2]);
-#pragma unroll
-              for (int q = 3; q < 31; q += 2) mn = fmin3g(mn, v[q], v[q + 1]);
-              mn = fminf(mn, v[31]);
-              mins[g][h] = mn;
-              atomicMin(&s_thr[p], __float_as_uint(mn + delta));
             }
+          }
+          release();
+        } else {
+          aborted = !ok;  // warp-uniform; the end-of-tile barrier makes it block-wide
+          if (aborted) break;
+          thr = fminf(thr, __uint_as_float(thr_sh[p]));
+          unsigned long long v[16];
+          float m0, m1;
+          chunk(0, v, m0, m1);
+          if (valid) {
+            keep(v, kb, m0);
+            keep(v + 8, kb + 16, m1);
+          }
+          chunk(1, v, m0, m1);
+          release();
+          if (valid) {
+            keep(v, kb + 32, m0);
+            keep(v + 8, kb + 48, m1);
+            atomicMin(&thr_sh[p], __float_as_uint(thr));
           }
         }
       }
-      __syncthreads();
-      if (ok) {
-        const float thr = __uint_as_float(s_thr[p]);
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          if (g < ng) {
-            const int nt = nt0 + g;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              // the warp reads the chunk when any of its points needs it
-              // (tcgen05.ld is warp-collective); each lane collects its own
-              const bool mine = mins[g][h] <= thr;
-              if (__any_sync(0xffffffffu, mine)) {
-                const int col = cslice * 64 + h * 32;
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((nt & 1) * kGN + col), v);
-                const int k0 = nt * kGN + col;
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                  const float r = __fmaf_rn(v[q], gc.scale, s_np[k0 + q]);
-                  if (mine && r <= thr) {
-                    const int slot = atomicAdd(&s_cnt[p], 1);
-                    if (slot < kGCand) {
-                      s_cand[p * kGCand + slot] = (uint32_t)(k0 + q);
-                      s_candr[p * kGCand + slot] = r;
-                    }
-                  }
-                }
-              }
-            }
-          }
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      aborted = __syncthreads_or(ok ? 0 : 1) != 0;  // block-uniform
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      __syncwarp();
+      aborted = epi_sync_or(aborted);  // all halves of the tile are stored
       if (aborted) break;
-      if (tid == 0)
-        for (int g = 0; g < 2; ++g)
-          if (nt0 + 2 + g < NT) issue(nt0 + 2 + g);
-    }
-    if (aborted) break;
-    // Resolve: 4 threads per point (16 coordinates each).  One candidate
-    // decides the label; otherwise the candidates (all K after an overflow)
-    // are ranked by the FP32 direct form summed over the 4 threads (its
-    // bound does not depend on the summation order), then, if that is not
-    // conclusive, in FP64 in the oracle's order by the point's first thread.
-    {
-      const int pp = tid >> 2, sub = tid & 3;
-      const unsigned gmask = 0xFu << (lane & ~3);
-      const int64_t i = (int64_t)tile * kGM + pp;
-      if (i < a.n) {
-        const float thr = __uint_as_float(s_thr[pp]);
-        const int nc = s_cnt[pp];
-        int nl = 0, only = -1;
-        if (nc <= kGCand)
-          for (int q = 0; q < nc; ++q)
-            if (s_candr[pp * kGCand + q] <= thr) { ++nl; only = (int)s_cand[pp * kGCand + q]; }
-        const bool over = nc > kGCand || nl == 0;  // scan all K (an empty list cannot happen; kept safe)
-        int lab = only;
-        if (over || nl != 1) {
-          const float* xrow = a.xaos + (size_t)i * kGemmD + sub * 16;
-          float xt[16];
-#pragma unroll
-          for (int q = 0; q < 16; q += 4) {
-            const float4 v = *reinterpret_cast<const float4*>(xrow + q);
-            xt[q] = __fsub_rn(v.x, s_shift[sub * 16 + q]);
-            xt[q + 1] = __fsub_rn(v.y, s_shift[sub * 16 + q + 1]);
-            xt[q + 2] = __fsub_rn(v.z, s_shift[sub * 16 + q + 2]);
-            xt[q + 3] = __fsub_rn(v.w, s_shift[sub * 16 + q + 3]);
-          }
-          const int m = over ? a.k : nc;
-          float best = 3.0e38f, second = 3.0e38f;
-          int kb = 0;
-#pragma unroll 4
-          for (int q = 0; q < m; ++q) {
-            int c;
-            bool use = true;
-            if (over) c = q;
-            else {
-              use = s_candr[pp * kGCand + q] <= thr;  // same decision on all 4 threads
-              c = (int)s_cand[pp * kGCand + q];
-            }
-            const float* crow = a.ctil + (size_t)c * kGemmD + sub * 16;
-            float part = 0.f;
-#pragma unroll
-            for (int j = 0; j < 16; j += 4) {
-              const float4 cv = *reinterpret_cast<const float4*>(crow + j);
-              float t = __fsub_rn(xt[j], cv.x); part = __fmaf_rn(t, t, part);
-              t = __fsub_rn(xt[j + 1], cv.y); part = __fmaf_rn(t, t, part);
-              t = __fsub_rn(xt[j + 2], cv.z); part = __fmaf_rn(t, t, part);
-              t = __fsub_rn(xt[j + 3], cv.w); part = __fmaf_rn(t, t, part);
-            }
-            part = __fadd_rn(part, __shfl_xor_sync(gmask, part, 1));
-            part = __fadd_rn(part, __shfl_xor_sync(gmask, part, 2));  // identical on the 4 threads
-            if (use) {
-              if (part < best || (part == best && c < kb)) { second = best; best = part; kb = c; }
-              else if (part < second) second = part;
-            }
-          }
-          if (sub == 0 && over) ++nover;
-          lab = kb;
-          const float A = a.xa[i];
-          const float sA = sqrtf(A), sB = sqrtf(gc.B_max), AB = A + gc.B_max;
-          const float e1 = bound64(best, sA, sB, AB), e2 = bound64(second, sA, sB, AB);
-          const float lo2 = second - e2, hi1 = best + e1;
-          const bool need64 = second < 3.0e38f && !((lo2 > hi1) && (lo2 - hi1 > gc.tau * (second + e2)));
-          if (need64 && sub == 0) {
-            const float* xr = a.xaos + (size_t)i * kGemmD;
-            double bd = 0.0;
-            int k64 = -1;
-            for (int q = 0; q < m; ++q) {
-              int c;
-              if (over) c = q;
-              else {
-                if (!(s_candr[pp * kGCand + q] <= thr)) continue;
-                c = (int)s_cand[pp * kGCand + q];
-              }
-              const double dd = d64row(xr, a.mu + (size_t)c * kGemmD);
-              if (k64 < 0 || dd < bd || (dd == bd && c < k64)) { bd = dd; k64 = c; }
-            }
-            lab = k64;
-            ++n64;
-          }
-          if (sub == 0) ++nflag;
+
+      // ---------------- resolve: 4 threads per point ----------------
+      // The stored values under the final threshold are the candidates.  One
+      // candidate is the label.  Up to kTieMax go to the near-tie list, more
+      // (or a point whose halves did not fit) to the rescue list; both are
+      // decided exactly by separate kernels.
+      {
+        const unsigned gmask = 0xFu << (lane & ~3);
+        const int64_t ii = tile * kGM + pp;
+        const int nc = es.cnt[pp];
+        const bool over = es.over[pp] != 0;
+        const int ns = min(nc, kSlots);
+        // per slot j: the values (16-bit q, see store_half) under the final
+        // threshold t are those with q <= qt_j = (bits(t) - bits(m_j)) / 2^8
+        const uint32_t tb = es.thr[par * kGM + pp];
+        const unsigned char* srow = es.store + pp * kPtStride + sub * 8;
+        auto slot_mask = [&](int j) {  // 4 bits: this thread's values of slot j under t
+          const uint32_t bm = es.smin[pp * kSlots + j];
+          if (tb < bm) return 0u;
+          const uint32_t qt = min((tb - bm) >> 8, 0xFFFFu);
+          const uint2 w = *reinterpret_cast<const uint2*>(srow + j * kHalf * 2);
+          const uint32_t c0 = __vcmpleu2(w.x, qt | (qt << 16)), c1 = __vcmpleu2(w.y, qt | (qt << 16));
+          return (c0 & 1u) | ((c0 >> 15) & 2u) | ((c1 & 1u) << 2) | ((c1 >> 13) & 8u);
+        };
+        int mine = 0;
+        for (int j = 0; j < ns; ++j) mine += __popc(slot_mask(j));
+        const int n1 = __shfl_xor_sync(0xffffffffu, mine, 1);  // sub ^ 1
+        const int n2 = __shfl_xor_sync(0xffffffffu, mine, 2);  // sub ^ 2
+        const int n3 = __shfl_xor_sync(0xffffffffu, n1, 2);    // sub ^ 3
+        const int tot = mine + n1 + n2 + n3;
+        // candidates of the point's threads with a lower sub
+        const int before = sub == 0 ? 0 : sub == 1 ? n1 : sub == 2 ? n2 + n3 : n1 + n2 + n3;
+        const bool live = ii < a.n;
+        // kind: 1 = decided here, 2 = near tie, 3 = rescue
+        const int kind = !live ? 0 : (over || tot == 0 || tot > kTieMax) ? 3 : tot == 1 ? 1 : 2;
+        // list slots, one atomic per warp and list
+        const bool lead = sub == 0;
+        const unsigned btie = __ballot_sync(0xffffffffu, lead && kind == 2);
+        const unsigned bres = __ballot_sync(0xffffffffu, lead && kind == 3);
+        unsigned base_t = 0, base_r = 0;
+        if (lane == 0) {
+          if (btie) base_t = atomicAdd(a.tie_count, (unsigned)__popc(btie));
+          if (bres) base_r = atomicAdd(a.rescue_count, (unsigned)__popc(bres));
         }
-        if (sub == 0) a.labels[i] = lab;
+        base_t = __shfl_sync(0xffffffffu, base_t, 0);
+        base_r = __shfl_sync(0xffffffffu, base_r, 0);
+        const unsigned below = (1u << lane) - 1u;
+        const unsigned entry = base_t + __popc(btie & ((1u << (lane & ~3)) - 1u));  // the point's entry
+        if ((kind == 1 || kind == 2) && mine > 0) {
+          // this thread's candidates: the label (one candidate in all) or
+          // its part of the near-tie entry
+          unsigned short* cl = reinterpret_cast<unsigned short*>(a.tie_list + 3 * (size_t)entry) + 4 + before;
+          int q = 0;
+          for (int j = 0; j < ns; ++j) {
+            uint32_t mm = slot_mask(j);
+            while (mm) {
+              const int bb = __ffs((int)mm) - 1;
+              mm &= mm - 1u;
+              const int c = es.sk[pp * kSlots + j] + sub * 4 + bb;
+              if (kind == 1) a.labels[ii] = c;
+              else cl[q++] = (unsigned short)c;
+            }
+          }
+        }
+        if (lead && kind == 2) {
+          *reinterpret_cast<int2*>(a.tie_list + 3 * (size_t)entry) = make_int2((int)ii, tot);
+          ++nflag;
+        }
+        if (lead && kind == 3) {
+          a.rescue_list[base_r + __popc(bres & below)] = (int32_t)ii;
+          ++nresc;
+        }
+        // the 4 threads have read the point's slots; clear them for the next
+        // tile (written again only after its first-group barrier)
+        __syncwarp();
+        if (lead) {
+          es.cnt[pp] = 0;
+          es.over[pp] = 0;
+          es.thr[par * kGM + pp] = 0x7f800000u;  // next used by tile l + 2
+#pragma unroll
+          for (int j = 0; j < kSlots; ++j) es.smin[pp * kSlots + j] = 0u;
+        }
       }
+      // the next tile's start threshold; the barrier publishes it and keeps
+      // the next tile's stores behind every read of this tile's slots
+      if (l + 1 < nloc) start_estimate(l + 1, nz, nA4);
+      curA = nA;
+      prefetch(l + 2);
+      __syncwarp();
+      aborted = epi_sync_or(aborted);
     }
-    // the next tile rewrites the per-point arrays after its first barrier
+    if (nflag) atomicAdd(&s_stat[0], nflag);
+    if (nresc) atomicAdd(&s_stat[2], nresc);
   }
-  // drain: every issued MMA group has been waited on unless aborted; if
-  // aborted, wait (bounded) for both accumulators before releasing TMEM
-  if (aborted) {
-    wait_bar(bar0, ph0);
-    wait_bar(bar1, ph1);
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  if (nflag) atomicAdd(&s_stat[0], nflag);
-  if (n64) atomicAdd(&s_stat[1], n64);
-  if (nover) atomicAdd(&s_stat[2], nover);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   if (tid == 0) {
     if (s_stat[0]) atomicAdd(&a.ls->flagged, (unsigned long long)s_stat[0]);
-    if (s_stat[1]) atomicAdd(&a.ls->fp64_decided, (unsigned long long)s_stat[1]);
-    if (s_stat[2]) atomicAdd(&a.ls->overflowed, (unsigned long long)s_stat[2]);
+    if (s_stat[2]) {
+      atomicAdd(&a.ls->overflowed, (unsigned long long)s_stat[2]);
+      atomicAdd(&a.ls->flagged, (unsigned long long)s_stat[2]);
+    }
   }
 }
 
-// Points -> BF16 shifted rows, ||x~||^2 (rounded up) and an N x d FP32 copy.
+// Near ties listed by the assign kernel (2..kTieMax candidates under the
+// final threshold): 4 threads per point (16 coordinates each) rank the
+// candidates by the FP32 direct form with its rigorous bound; when that is
+// not conclusive, the first thread decides in FP64 in the oracle's order
+// (lowest index on ties).
+__global__ void __launch_bounds__(256) gemm_tie_kernel(GemmArgs a) {
+  if (a.ls->done) return;
+  const unsigned cnt = *a.tie_count;
+  const GemmConst gc = *a.gc;
+  const int lane = threadIdx.x & 31, sub = lane & 3;
+  const unsigned gmask = 0xFu << (lane & ~3);
+  const unsigned groups = gridDim.x * (blockDim.x / 4);
+  int n64 = 0;
+  for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) / 4; e < cnt; e += groups) {
+    const int4* ent = a.tie_list + 3 * (size_t)e;
+    const int2 h0 = *reinterpret_cast<const int2*>(ent);
+    const int64_t ii = h0.x;
+    const int nc = h0.y;
+    const unsigned short* cl = reinterpret_cast<const unsigned short*>(ent) + 4;
+    auto cand = [&](int q) { return (int)cl[q]; };
+    const float* xrow = a.xaos + (size_t)ii * kGemmD + sub * 16;
+    float xt[16];
+#pragma unroll
+    for (int q = 0; q < 16; q += 4) {
+      const float4 xv = *reinterpret_cast<const float4*>(xrow + q);
+      const float4 sv = *reinterpret_cast<const float4*>(a.shift + sub * 16 + q);
+      xt[q] = __fsub_rn(xv.x, sv.x);
+      xt[q + 1] = __fsub_rn(xv.y, sv.y);
+      xt[q + 2] = __fsub_rn(xv.z, sv.z);
+      xt[q + 3] = __fsub_rn(xv.w, sv.w);
+    }
+    float best = 3.0e38f, second = 3.0e38f;
+    int kbest = 0;
+    for (int q = 0; q < nc; ++q) {
+      const int c = cand(q);
+      if (c >= a.k) continue;  // padding column (same on the 4 threads)
+      const float* crow = a.ctil + (size_t)c * kGemmD + sub * 16;
+      float part = 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; j += 4) {
+        const float4 cv = *reinterpret_cast<const float4*>(crow + j);
+        float u = __fsub_rn(xt[j], cv.x); part = __fmaf_rn(u, u, part);
+        u = __fsub_rn(xt[j + 1], cv.y); part = __fmaf_rn(u, u, part);
+        u = __fsub_rn(xt[j + 2], cv.z); part = __fmaf_rn(u, u, part);
+        u = __fsub_rn(xt[j + 3], cv.w); part = __fmaf_rn(u, u, part);
+      }
+      part = __fadd_rn(part, __shfl_xor_sync(gmask, part, 1));
+      part = __fadd_rn(part, __shfl_xor_sync(gmask, part, 2));  // identical on the 4 threads
+      if (part < best || (part == best && c < kbest)) { second = best; best = part; kbest = c; }
+      else if (part < second) second = part;
+    }
+    int lab = kbest;
+    const float A = a.xa[ii];
+    const float sA = sqrtf(A), sB = sqrtf(gc.B_max), AB = A + gc.B_max;
+    const float e1 = bound64(best, sA, sB, AB), e2 = bound64(second, sA, sB, AB);
+    const float lo2 = second - e2, hi1 = best + e1;
+    const bool need64 = !((lo2 > hi1) && (lo2 - hi1 > gc.tau * (second + e2)));
+    if (sub == 0) {
+      if (need64) {
+        const float* xr = a.xaos + (size_t)ii * kGemmD;
+        double bd = 0.0;
+        int k64 = -1;
+        for (int q = 0; q < nc; ++q) {
+          const int c = cand(q);
+          if (c >= a.k) continue;
+          const double dd = d64row(xr, a.mu + (size_t)c * kGemmD);
+          if (k64 < 0 || dd < bd || (dd == bd && c < k64)) { bd = dd; k64 = c; }
+        }
+        lab = k64;
+        ++n64;
+      }
+      a.labels[ii] = lab;
+    }
+  }
+  if (sub == 0 && n64) atomicAdd(&a.ls->fp64_decided, (unsigned long long)n64);
+}
+
+// Exact argmin over all K for the points listed by the assign kernel: one
+// warp per point, lane l takes centroids l, l + 32, ...: FP32 direct form
+// with its bound, then FP64 in the oracle's order over every centroid whose
+// lower bound is not above the best upper bound (lowest index on ties).
+__global__ void __launch_bounds__(256) gemm_rescue_kernel(GemmArgs a) {
+  __shared__ float s_x[8][kGemmD];
+  if (a.ls->done) return;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned cnt = *a.rescue_count;
+  const GemmConst gc = *a.gc;
+  int n64 = 0;
+  for (unsigned e = blockIdx.x * 8u + w; e < cnt; e += gridDim.x * 8u) {
+    const int64_t i = a.rescue_list[e];
+    const float* xr = a.xaos + (size_t)i * kGemmD;
+    s_x[w][lane] = __fsub_rn(xr[lane], a.shift[lane]);
+    s_x[w][lane + 32] = __fsub_rn(xr[lane + 32], a.shift[lane + 32]);
+    __syncwarp();
+    const float A = a.xa[i];
+    const float sA = sqrtf(A), sB = sqrtf(gc.B_max), AB = A + gc.B_max;
+    float dv[kGemmMaxK / 32];
+    float best = 3.0e38f;
+#pragma unroll
+    for (int t = 0; t < kGemmMaxK / 32; ++t) {
+      const int c = lane + 32 * t;
+      dv[t] = 3.0e38f;
+      if (c < a.k) {
+        const float* crow = a.ctil + (size_t)c * kGemmD;
+        float acc = 0.f;
+        for (int j = 0; j < kGemmD; j += 4) {
+          const float4 cv = *reinterpret_cast<const float4*>(crow + j);
+          float u = __fsub_rn(s_x[w][j], cv.x); acc = __fmaf_rn(u, u, acc);
+          u = __fsub_rn(s_x[w][j + 1], cv.y); acc = __fmaf_rn(u, u, acc);
+          u = __fsub_rn(s_x[w][j + 2], cv.z); acc = __fmaf_rn(u, u, acc);
+          u = __fsub_rn(s_x[w][j + 3], cv.w); acc = __fmaf_rn(u, u, acc);
+        }
+        dv[t] = acc;
+        best = fminf(best, acc);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    const float hi1 = best + bound64(best, sA, sB, AB);
+    double bd = 0.0;
+    int k64 = -1;
+#pragma unroll
+    for (int t = 0; t < kGemmMaxK / 32; ++t) {
+      const int c = lane + 32 * t;
+      if (c < a.k && dv[t] - bound64(dv[t], sA, sB, AB) <= hi1) {
+        const double dd = d64row(xr, a.mu + (size_t)c * kGemmD);
+        if (k64 < 0 || dd < bd || (dd == bd && c < k64)) { bd = dd; k64 = c; }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, bd, o);
+      const int ok = __shfl_xor_sync(0xffffffffu, k64, o);
+      if (ok >= 0 && (k64 < 0 || ob < bd || (ob == bd && ok < k64))) { bd = ob; k64 = ok; }
+    }
+    if (lane == 0) {
+      a.labels[i] = k64;
+      ++n64;
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && n64) atomicAdd(&a.ls->fp64_decided, (unsigned long long)n64);
+}
+
+// Points -> BF16 shifted rows in the swizzled tile layout, ||x~||^2 (rounded
+// up) and an N x d FP32 copy.
 __global__ void gemm_prep_points_kernel(const float* __restrict__ x, int64_t ld, int64_t n, const float* shift,
                                         __nv_bfloat16* xb, float* xa, float* xaos) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -448,20 +748,20 @@ __global__ void gemm_prep_points_kernel(const float* __restrict__ x, int64_t ld,
       const float v = x[(int64_t)j * ld + i];
       const float t = __fsub_rn(v, shift[j]);
       xaos[i * kGemmD + j] = v;
-      xb[i * kGemmD + j] = __float2bfloat16_rn(t);
+      xb[swz_index(i, j)] = __float2bfloat16_rn(t);
       A = __fmaf_ru(t, t, A);
     }
     xa[i] = A;
   }
 }
 
-// Tables of the next step from mu (one block): BF16 centroid rows, n'_k,
-// FP32 c~ rows, the scale and the candidate-window constants.
+// Tables of the next step from mu (one block): BF16 centroid rows in the
+// swizzled layout, n'_k, FP32 c~ rows, the scale and the window constants.
 __global__ void __launch_bounds__(256) gemm_prepare_kernel(GemmPrepArgs a) {
   __shared__ double s_b[1024];
-  __shared__ double s_bmax;
   __shared__ int s_sigma;
   const int k = a.k, kpad = a.kpad;
+  __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(a.cb);
   for (int c = threadIdx.x; c < kpad; c += blockDim.x) {
     double B = 0.0;
     for (int j = 0; j < kGemmD; ++j) {
@@ -472,7 +772,7 @@ __global__ void __launch_bounds__(256) gemm_prepare_kernel(GemmPrepArgs a) {
         a.ctil[(size_t)c * kGemmD + j] = cv;
         B = __dadd_rn(B, __dmul_rn(t, t));
       }
-      reinterpret_cast<__nv_bfloat16*>(a.cb)[(size_t)c * kGemmD + j] = __float2bfloat16_rn(cv);
+      cb[swz_index(c, j)] = __float2bfloat16_rn(cv);
     }
     if (c < 1024) s_b[c] = c < k ? B : 0.0;
   }
@@ -480,7 +780,6 @@ __global__ void __launch_bounds__(256) gemm_prepare_kernel(GemmPrepArgs a) {
   if (threadIdx.x == 0) {
     double bmax = 0.0;
     for (int c = 0; c < k; ++c) bmax = fmax(bmax, s_b[c]);
-    s_bmax = bmax;
     const double P = 1.02 * ((double)a.A_max + 2.0 * bmax) + 1e-300;
     const double top = 0.5;  // binade [1, 2): M = 1.5, |2^sigma (h - 2S)| < 0.5
     int sigma = ilogb(top / P);
@@ -500,8 +799,9 @@ __global__ void __launch_bounds__(256) gemm_prepare_kernel(GemmPrepArgs a) {
     g.c0 = (float)((tw * (2.0 * u * bmax + gam * bmax + a.tie_rel * bmax) + 8.0 * 0x1p-23) * (1.0 + 1e-3));
     g.c1 = (float)(tw * (4.0 * epsS * sB + 2.0 * a.tie_rel * sB) * (1.0 + 1e-3));
     g.cA = (float)(tw * (gam + a.tie_rel) * (1.0 + 1e-3));
-    // start estimate (FP32 dot product in another order): 2^(sigma+1) 2^-17 ||x~|| ||c~|| + 2 ulps
-    g.cest = (float)(2.0 * tw * 0x1p-17 * sB * 1.02 + 0.0);
+    // start estimate: |r_est - r_tc| <= 2^(sigma+1) (2^-16 + 2^-18) ||x_b|| ||c_b|| (two FP32
+    // sums of 64 BF16 products in different orders), taken as 2^-14 per unit ||x~||
+    g.cest = (float)(2.0 * tw * 0x1p-14 * sB);
     g.B_max = (float)(bmax * (1.0 + 1e-6));
     g.tau = (float)(a.tie_rel * (1.0 + 1e-4));
     g.pad0 = g.pad1 = 0.f;
@@ -509,27 +809,41 @@ __global__ void __launch_bounds__(256) gemm_prepare_kernel(GemmPrepArgs a) {
   }
   __syncthreads();
   const double tw = ldexp(1.0, s_sigma);
+  // padding columns: r = 4, far above any real r < 2 plus the window
   for (int c = threadIdx.x; c < kpad; c += blockDim.x)
-    a.nprime[c] = c < k ? __double2float_rn(1.5 + tw * s_b[c]) : 1.99999988f;  // padding: top of the binade
+    a.nprime[c] = c < k ? __double2float_rn(1.5 + tw * s_b[c]) : 4.0f;
 }
 
 }  // namespace
 
 size_t gemm_smem_bytes(int kpad) {
-  return 1024 + (size_t)kpad * 128 + 2 * kGM * 128 + (size_t)kpad * 4 + kGM * 4 * 2 + (size_t)kGM * kGCand * 8 +
-         kGM * 4 + kGemmD * 4 + 16 + 32;
+  return 1024 + (size_t)kOffOperands + (size_t)kpad * 128 + 2 * kTileBytes + (size_t)kpad * 4;
 }
+
+int64_t gemm_xb_rows(int64_t n) { return (n + kGM - 1) / kGM * kGM; }
 
 cudaError_t launch_gemm_assign(int grid, cudaStream_t st, const GemmArgs& a) {
   const size_t smem = gemm_smem_bytes(a.kpad);
   cudaError_t e = cudaFuncSetAttribute(gemm_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // rescue_count and tie_count are adjacent: one memset clears both
+  e = cudaMemsetAsync(a.rescue_count, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
   gemm_assign_kernel<<<grid, kGThreads, smem, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gemm_tie_kernel<<<grid * 8, 256, 0, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gemm_rescue_kernel<<<grid * 4, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_prep_points(const float* x, int64_t ld, int64_t n, const float* shift, void* xb, float* xa,
                                     float* xaos, cudaStream_t st) {
+  // rows past N (to the next tile boundary) stay zero
+  cudaError_t e = cudaMemsetAsync(xb, 0, (size_t)gemm_xb_rows(n) * kGemmD * 2, st);
+  if (e != cudaSuccess) return e;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
   gemm_prep_points_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, ld, n, shift, reinterpret_cast<__nv_bfloat16*>(xb),
                                                             xa, xaos);

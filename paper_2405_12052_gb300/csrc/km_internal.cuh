@@ -144,17 +144,21 @@ struct GemmConst {
 };
 
 struct GemmArgs {
-  const void* xb;        // [N][64] BF16 rows of fl(x - s)  (__nv_bfloat16)
+  const void* xb;        // [ceil(N/128)*128][64] BF16 rows of fl(x - s), 128-byte swizzled (__nv_bfloat16)
   const float* xa;       // [N] ||fl(x - s)||^2, rounded up
   const float* xaos;     // [N][64] FP32 points
-  const void* cb;        // [kpad][64] BF16 rows of fl(mu - s)
+  const void* cb;        // [kpad][64] BF16 rows of fl(mu - s), 128-byte swizzled
   const float* nprime;   // [kpad] n'_k = fl(M + 2^sigma ||mu_k - s||^2)
   const float* ctil;     // [k][64] fl32(mu - s)
   const double* mu;      // [k][64]
   const float* shift;    // [64]
   const GemmConst* gc;
   LoopState* ls;
-  int32_t* labels;       // in: previous labels (start estimate); out: labels
+  int32_t* labels;       // out: labels
+  int32_t* rescue_list;  // [N] points resolved over all K by the rescue kernel
+  int4* tie_list;        // [N][3] near ties: point, count, up to 20 16-bit candidates
+  unsigned* rescue_count;  // [0] rescue entries, [1] near-tie entries
+  unsigned* tie_count;     // = rescue_count + 1
   int64_t n;
   int k, kpad, ntiles;
 };
@@ -186,6 +190,7 @@ cudaError_t launch_gemm_prep_points(const float* x, int64_t ld, int64_t n, const
                                     float* xaos, cudaStream_t st);
 cudaError_t launch_gemm_prepare(cudaStream_t st, const GemmPrepArgs& a);
 size_t gemm_smem_bytes(int kpad);
+int64_t gemm_xb_rows(int64_t n);
 int64_t msort_max_chunks(int64_t n, int k);
 cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st);
 

@@ -86,3 +86,15 @@ def test_gemm_full_scale_sampled(km, oracle):
     st = g.stats()
     assert st["path"] == 3
     g.close()
+
+
+def test_gemm_duplicate_centroids_near_tie_and_rescue_lists(km, oracle):
+    """Exact duplicates: 12 copies of one centre (a near tie with more
+    candidates than one list entry of 8 would hold) and 30 copies of another
+    (more than a near-tie entry holds: the all-K rescue).  The oracle takes
+    the lowest index among equal distances; so must the GPU."""
+    x, _, _ = synth.iso_mixture(20_000, 64, 30, sigma=1.0, box=10.0, seed=11)
+    base, _ = synth.init_distinct(x, 40, seed=12)
+    mu0 = np.concatenate([base, np.repeat(base[:1], 12, 0), np.repeat(base[1:2], 30, 0)])
+    st = lockstep(km, oracle, x, mu0, steps=2)
+    assert st["path"] == 3 and st["flagged"] > 0
