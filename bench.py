@@ -339,7 +339,7 @@ def run_ours(args, ws, rank, local):
                               else "seeded distinct points",
                       "l2": "points 1.2 GB > 129 MB L2: no flush needed" if n * d * 4 > 129e6 else "L2-resident",
                       "parallelism": "single" if ws == 1 else f"replicas{ws}"},
-           "clocks": clk, "e2e": e2e, "gpu_launches": (8 if stats["path"] == 3 else 2) * K, "roofline": roof,
+           "clocks": clk, "e2e": e2e, "gpu_launches": (11 if stats["path"] == 3 else 2) * K, "roofline": roof,
            "assign_ms": assign_ms, "update_ms": ms_step - assign_ms,
            "flagged_per_step": stats["flagged"], "fp64_decided_per_step": stats["fp64_decided"],
            "overflowed_per_step": stats["overflowed"],

@@ -67,6 +67,8 @@ struct km_ctx {
   int* ms_nchunks = nullptr;
   long long* ms_chunk_sums = nullptr;
   int32_t* ms_perm = nullptr;
+  double* ms_df2 = nullptr;
+  double* bnorm = nullptr;
   int ms_max_chunks = 0;
   float A_max = 0.f;
   int G0 = 0;
@@ -104,7 +106,7 @@ void free_all(km_ctx* c) {
                   c->ctil4, c->ctil, c->cnorm, c->shift, c->gen_bmax, c->dc, c->ic, c->ls,
                   c->scan, c->scan_bad, c->xb, c->xa_pt, c->xaos, c->cbf, c->nprime, c->gc,
                   c->ms_counts, c->ms_offsets, c->ms_cfirst, c->ms_cursor, c->ms_chunks, c->ms_nchunks,
-                  c->ms_chunk_sums, c->ms_perm, c->rescue_list, c->tie_list, c->rescue_count};
+                  c->ms_chunk_sums, c->ms_perm, c->rescue_list, c->tie_list, c->rescue_count, c->ms_df2, c->bnorm};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -126,7 +128,7 @@ GemmPrepArgs gemm_prep_args(km_ctx* c) {
   GemmPrepArgs g{};
   g.mu = c->mu; g.shift = c->shift; g.k = c->k; g.kpad = c->kpad;
   g.cb = c->cbf; g.nprime = c->nprime; g.ctil = c->ctil; g.gc = c->gc;
-  g.A_max = c->A_max; g.tie_rel = c->opt.tie_rel; g.ls = c->ls;
+  g.A_max = c->A_max; g.tie_rel = c->opt.tie_rel; g.ls = c->ls; g.bnorm = c->bnorm;
   return g;
 }
 
@@ -136,6 +138,7 @@ MsortArgs msort_args(km_ctx* c) {
   m.counts_u = c->ms_counts; m.offsets = c->ms_offsets; m.cfirst = c->ms_cfirst; m.cursor = c->ms_cursor;
   m.chunks = c->ms_chunks; m.nchunks = c->ms_nchunks; m.max_chunks = c->ms_max_chunks;
   m.chunk_sums = c->ms_chunk_sums; m.perm = c->ms_perm; m.mu = c->mu; m.counts = c->counts; m.ls = c->ls;
+  m.df2 = c->ms_df2;
   return m;
 }
 
@@ -320,6 +323,8 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
     KM_CUDA(c, dalloc(&c->ms_nchunks, 1));
     KM_CUDA(c, dalloc(&c->ms_chunk_sums, (size_t)c->ms_max_chunks * d));
     KM_CUDA(c, dalloc(&c->ms_perm, (size_t)n));
+    KM_CUDA(c, dalloc(&c->ms_df2, (size_t)k * d));
+    KM_CUDA(c, dalloc(&c->bnorm, (size_t)c->kpad));
   }
   KM_CUDA(c, cudaMemsetAsync(c->ls, 0, sizeof(LoopState), c->st));
   KM_CUDA(c, cudaMemsetAsync(c->counts, 0, sizeof(long long) * k, c->st));

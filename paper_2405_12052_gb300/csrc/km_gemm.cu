@@ -755,31 +755,42 @@ __global__ void gemm_prep_points_kernel(const float* __restrict__ x, int64_t ld,
   }
 }
 
-// Tables of the next step from mu (one block): BF16 centroid rows in the
-// swizzled layout, n'_k, FP32 c~ rows, the scale and the window constants.
-__global__ void __launch_bounds__(256) gemm_prepare_kernel(GemmPrepArgs a) {
-  __shared__ double s_b[1024];
+// Tables of the next step from mu, one thread per centroid: BF16 rows in the
+// swizzled layout, FP32 c~ rows and B_k = ||mu_k - s||^2 (FP64, coordinates
+// in order).
+__global__ void __launch_bounds__(64) gemm_tables_kernel(GemmPrepArgs a) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.kpad) return;
+  __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(a.cb);
+  double B = 0.0;
+  for (int j = 0; j < kGemmD; ++j) {
+    float cv = 0.f;
+    if (c < a.k) {
+      const double t = __dsub_rn(a.mu[(size_t)c * kGemmD + j], (double)a.shift[j]);
+      cv = __double2float_rn(t);
+      a.ctil[(size_t)c * kGemmD + j] = cv;
+      B = __dadd_rn(B, __dmul_rn(t, t));
+    }
+    cb[swz_index(c, j)] = __float2bfloat16_rn(cv);
+  }
+  a.bnorm[c] = c < a.k ? B : 0.0;
+}
+
+// The scale and window constants from max_k B_k (one block), then n'_k.
+__global__ void __launch_bounds__(256) gemm_consts_kernel(GemmPrepArgs a) {
+  __shared__ double s_max[256];
   __shared__ int s_sigma;
   const int k = a.k, kpad = a.kpad;
-  __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(a.cb);
-  for (int c = threadIdx.x; c < kpad; c += blockDim.x) {
-    double B = 0.0;
-    for (int j = 0; j < kGemmD; ++j) {
-      float cv = 0.f;
-      if (c < k) {
-        const double t = __dsub_rn(a.mu[(size_t)c * kGemmD + j], (double)a.shift[j]);
-        cv = __double2float_rn(t);
-        a.ctil[(size_t)c * kGemmD + j] = cv;
-        B = __dadd_rn(B, __dmul_rn(t, t));
-      }
-      cb[swz_index(c, j)] = __float2bfloat16_rn(cv);
-    }
-    if (c < 1024) s_b[c] = c < k ? B : 0.0;
-  }
+  double m = 0.0;
+  for (int c = threadIdx.x; c < k; c += blockDim.x) m = fmax(m, a.bnorm[c]);
+  s_max[threadIdx.x] = m;
   __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + w]);
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    double bmax = 0.0;
-    for (int c = 0; c < k; ++c) bmax = fmax(bmax, s_b[c]);
+    const double bmax = s_max[0];
     const double P = 1.02 * ((double)a.A_max + 2.0 * bmax) + 1e-300;
     const double top = 0.5;  // binade [1, 2): M = 1.5, |2^sigma (h - 2S)| < 0.5
     int sigma = ilogb(top / P);
@@ -811,7 +822,7 @@ __global__ void __launch_bounds__(256) gemm_prepare_kernel(GemmPrepArgs a) {
   const double tw = ldexp(1.0, s_sigma);
   // padding columns: r = 4, far above any real r < 2 plus the window
   for (int c = threadIdx.x; c < kpad; c += blockDim.x)
-    a.nprime[c] = c < k ? __double2float_rn(1.5 + tw * s_b[c]) : 4.0f;
+    a.nprime[c] = c < k ? __double2float_rn(1.5 + tw * a.bnorm[c]) : 4.0f;
 }
 
 }  // namespace
@@ -851,7 +862,10 @@ cudaError_t launch_gemm_prep_points(const float* x, int64_t ld, int64_t n, const
 }
 
 cudaError_t launch_gemm_prepare(cudaStream_t st, const GemmPrepArgs& a) {
-  gemm_prepare_kernel<<<1, 256, 0, st>>>(a);
+  gemm_tables_kernel<<<(a.kpad + 63) / 64, 64, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gemm_consts_kernel<<<1, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -166,6 +166,7 @@ struct GemmArgs {
 struct GemmPrepArgs {
   const double* mu; const float* shift; int k, kpad;
   void* cb; float* nprime; float* ctil; GemmConst* gc;
+  double* bnorm;                   // [kpad] ||mu_k - s||^2
   float A_max; double tie_rel;
   const LoopState* ls;
 };
@@ -181,6 +182,7 @@ struct MsortArgs {
   int4* chunks; int* nchunks; int max_chunks;
   long long* chunk_sums;           // [max_chunks][d]
   int32_t* perm;                   // [N]
+  double* df2;                     // [k][d] squared centroid moves
   double* mu; long long* counts;   // out
   LoopState* ls;
 };

@@ -6,9 +6,9 @@
 // most kChunk points, every chunk is summed exactly in fixed point by one
 // block reading whole rows of the N x d copy of the points (coalesced), and
 // the finalize kernel adds each cluster's chunk sums in order in int128,
-// divides, keeps empty centres and forms E^2 by a fixed-order tree.  The
-// scatter order inside a cluster is not deterministic, but integer sums do
-// not depend on it.
+// divides and keeps empty centres; a one-block kernel forms E^2 by a
+// fixed-order tree.  The scatter order inside a cluster is not
+// deterministic, but integer sums do not depend on it.
 #include "km_internal.cuh"
 
 namespace km {
@@ -101,17 +101,24 @@ __global__ void ms_chunk_sum_kernel(const float* __restrict__ xa, int d, const i
   const DataConst dc = *dcp;
   long long acc = 0;
   if (r < R) {
-    for (int p = r; p < cd.z; p += R) {
-      const int i = perm[cd.y + p];
-      const float v = xa[(int64_t)i * d + j];
+    auto fixed = [&](float v) {  // v in grid units of 2^G0, exactly (two FP32 limbs)
       const float t = __fadd_rn(v, dc.C_hi);
       const float h = __fsub_rn(t, dc.C_hi);
       const float rr = __fsub_rn(v, h);
       const float t2 = __fadd_rn(rr, dc.C_lo);
       const long long hi = (long long)(int)(__float_as_uint(t) - dc.bits_C_hi);
       const long long lo = (long long)(int)(__float_as_uint(t2) - dc.bits_C_lo);
-      acc += (hi << 22) + lo;
+      return (hi << 22) + lo;
+    };
+    // four rows in flight per thread (integer sums do not depend on order)
+    int p = r;
+    for (; p + 3 * R < cd.z; p += 4 * R) {
+      const int i0 = perm[cd.y + p], i1 = perm[cd.y + p + R], i2 = perm[cd.y + p + 2 * R], i3 = perm[cd.y + p + 3 * R];
+      const float v0 = xa[(int64_t)i0 * d + j], v1 = xa[(int64_t)i1 * d + j];
+      const float v2 = xa[(int64_t)i2 * d + j], v3 = xa[(int64_t)i3 * d + j];
+      acc += fixed(v0) + fixed(v1) + fixed(v2) + fixed(v3);
     }
+    for (; p < cd.z; p += R) acc += fixed(xa[(int64_t)perm[cd.y + p] * d + j]);
     s_part[r * d + j] = acc;
   }
   __syncthreads();
@@ -141,47 +148,52 @@ __device__ __forceinline__ double ms_i128_to_double(unsigned long long lo, long 
   return neg ? -r : r;
 }
 
-// One block: per (cluster, coordinate), the cluster's chunk sums added in
-// chunk order in int128, one conversion, the divide; E^2 by a fixed-order
-// tree; the stop test.  Centroid tables for the next step are written by the
-// path's own prepare kernel afterwards.
-__global__ void __launch_bounds__(1024) ms_finalize_kernel(const unsigned long long* counts, const int* cfirst,
-                                                           const long long* chunk_sums, int k, int d,
-                                                           const DataConst* dcp, double* mu, long long* counts_out,
-                                                           LoopState* ls) {
+// One thread per (cluster, coordinate): the cluster's chunk sums added in
+// chunk order in int128, one conversion, the divide (an empty cluster keeps
+// its centre) and the squared move.  Centroid tables for the next step are
+// written by the path's own prepare kernels afterwards.
+__global__ void __launch_bounds__(256) ms_finalize_kernel(const unsigned long long* counts, const int* cfirst,
+                                                          const long long* chunk_sums, int k, int d,
+                                                          const DataConst* dcp, double* mu, long long* counts_out,
+                                                          double* df2, const LoopState* ls) {
+  if (ls->done) return;  // the loop already stopped (graph-driven runs)
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= k * d) return;
+  const int c = q / d, j = q - c * d;
+  const long long cnt = (long long)counts[c];
+  const long long first = cfirst[c];  // index of the cluster's first chunk (from the scan)
+  const int nch = (int)((cnt + kChunk - 1) / kChunk);
+  unsigned long long lo = 0ull;
+  long long hi = 0ll;
+  for (int t = 0; t < nch; ++t) {
+    const long long v = chunk_sums[(size_t)(first + t) * d + j];
+    const unsigned long long nl = lo + (unsigned long long)v;
+    hi += (v < 0 ? -1ll : 0ll) + (nl < lo ? 1ll : 0ll);
+    lo = nl;
+  }
+  const double old = mu[q];
+  double nw = old;
+  if (cnt > 0) nw = __ddiv_rn(ldexp(ms_i128_to_double(lo, hi), dcp->G0), (double)cnt);
+  const double df = __dsub_rn(nw, old);
+  df2[q] = __dmul_rn(df, df);
+  mu[q] = nw;
+  if (j == 0) counts_out[c] = cnt;
+}
+
+// One block: E^2 = sum of the squared moves by a fixed-order tree (thread t
+// adds entries t, t + 1024, ... in order), the empty-cluster count, the stop
+// test and the per-step statistics.
+__global__ void __launch_bounds__(1024) ms_close_kernel(const double* df2, int kd, const long long* counts, int k,
+                                                        LoopState* ls) {
   __shared__ double s_red[1024];
   __shared__ int s_empty;
-  if (ls->done) return;  // the loop already stopped (graph-driven runs)
+  if (ls->done) return;
   const int tid = threadIdx.x;
   if (tid == 0) s_empty = 0;
-  __syncthreads();
-  const int G0 = dcp->G0;
   double e2p = 0.0;
+  for (int q = tid; q < kd; q += blockDim.x) e2p = __dadd_rn(e2p, df2[q]);
   int empty = 0;
-  for (int q = tid; q < k * d; q += blockDim.x) {
-    const int c = q / d, j = q - c * d;
-    const long long cnt = (long long)counts[c];
-    const long long first = cfirst[c];  // index of the cluster's first chunk (from the scan)
-    const int nch = (int)((cnt + kChunk - 1) / kChunk);
-    unsigned long long lo = 0ull;
-    long long hi = 0ll;
-    for (int t = 0; t < nch; ++t) {
-      const long long v = chunk_sums[(size_t)(first + t) * d + j];
-      const unsigned long long nl = lo + (unsigned long long)v;
-      hi += (v < 0 ? -1ll : 0ll) + (nl < lo ? 1ll : 0ll);
-      lo = nl;
-    }
-    const double old = mu[q];
-    double nw = old;
-    if (cnt > 0) nw = __ddiv_rn(ldexp(ms_i128_to_double(lo, hi), G0), (double)cnt);
-    const double df = __dsub_rn(nw, old);
-    e2p = __dadd_rn(e2p, __dmul_rn(df, df));
-    mu[q] = nw;
-    if (j == 0) {
-      counts_out[c] = cnt;
-      empty += cnt == 0;
-    }
-  }
+  for (int c = tid; c < k; c += blockDim.x) empty += counts[c] == 0;
   s_red[tid] = e2p;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -226,7 +238,9 @@ cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st) {
   const int threads = R * a.d <= 1024 ? R * a.d : a.d;
   ms_chunk_sum_kernel<<<(unsigned)a.max_chunks, threads, sizeof(long long) * (size_t)std::max(1, threads / a.d) * a.d, st>>>(
       a.xa, a.d, a.perm, a.chunks, a.nchunks, a.dc, a.chunk_sums);
-  ms_finalize_kernel<<<1, 1024, 0, st>>>(a.counts_u, a.cfirst, a.chunk_sums, a.k, a.d, a.dc, a.mu, a.counts, a.ls);
+  ms_finalize_kernel<<<(a.k * a.d + 255) / 256, 256, 0, st>>>(a.counts_u, a.cfirst, a.chunk_sums, a.k, a.d, a.dc,
+                                                              a.mu, a.counts, a.df2, a.ls);
+  ms_close_kernel<<<1, 1024, 0, st>>>(a.df2, a.k * a.d, a.counts, a.k, a.ls);
   return cudaGetLastError();
 }
 
