@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batch workloads")
+    ap.add_argument("--plain-every", type=int, default=1,
+                    help="batch workloads: time plain km_run on every m-th instance (scaled up)")
     return ap.parse_args()
 
 
@@ -354,11 +357,105 @@ def run_ours(args, ws, rank, local):
     return 0
 
 
+def _gen_instance(a):
+    import synth
+    i, n, d, k = a
+    return synth.batch_instance(i, n, d, k)
+
+
+def gen_batch(count, seed=0):
+    """The batched workload, generated in a spawned process pool (before any
+    CUDA call)."""
+    import multiprocessing as mp
+    import synth
+    ns, ds, ks = synth.batch_sizes(count, seed)
+    jobs = [(i, int(ns[i]), int(ds[i]), int(ks[i])) for i in range(count)]
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        return pool.map(_gen_instance, jobs, chunksize=8)
+
+
+def run_batch(args, ws, rank, local):
+    """Batched form: all instances to convergence (tol 1e-6, max 300) in one
+    batch, against the same instances run one after another with plain
+    km_run on the same GPU (setup of each context not timed)."""
+    import numpy as np
+    t0 = time.perf_counter()
+    insts = gen_batch(args.batch_count)
+    gen_s = time.perf_counter() - t0
+    import torch
+    import paper_2405_12052_gb300 as km
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    km.build()
+    ns = np.array([w["n"] for w in insts]); ds = np.array([w["d"] for w in insts]); ks = np.array([w["k"] for w in insts])
+    flat = np.concatenate([w["x"].reshape(-1) for w in insts])
+    mus = np.concatenate([w["mu0"].reshape(-1) for w in insts])
+    b = km.KMeansBatch(ns, ds, ks)
+    b.set_points(torch.from_numpy(flat).to(dev))
+    b.set_init(mus)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    tile, thr = b.tune()
+    tune_s = time.perf_counter() - t0
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    r = b.run(300, 1e-6, want_labels=False)
+    torch.cuda.synchronize(dev)
+    batch_s = time.perf_counter() - t0
+    clk = clocks.stop()
+    info = b.info()
+    iters = r["iters"].astype(np.int64)
+    evals = float(np.sum(ns * ks * iters))
+    mu_batch = b.split_centroids(r["centroids"])
+    b.close()
+    # plain km_run, one instance after another
+    sel = list(range(0, len(insts), max(1, args.plain_every)))
+    plain_s = 0.0
+    same = True
+    plain_iters = 0
+    for i in sel:
+        w = insts[i]
+        g = km.KMeans(w["n"], w["d"], w["k"])
+        g.set_points(w["x"])
+        g.set_init(w["mu0"])
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        rr = g.run(300, 1e-6, want_labels=False)
+        plain_s += time.perf_counter() - t1
+        same = same and rr["iters"] == int(iters[i]) and np.array_equal(rr["centroids"], mu_batch[i])
+        plain_iters += rr["iters"]
+        g.close()
+    scale = len(insts) / len(sel)
+    out = {"metric": METRIC, "value": evals / batch_s, "unit": UNIT, "n_gpus": 1, "steps": int(iters.max()),
+           "warmup": 0, "ms_per_step": 1e3 * batch_s / max(1, int(iters.max())), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batch_{len(insts)}", "instances": len(insts), "points": int(ns.sum()),
+                      "n_range": [int(ns.min()), int(ns.max())], "d": [2, 3], "k_range": [int(ks.min()), int(ks.max())],
+                      "init": "seeded distinct points per instance", "tol": 1e-6, "max_iter": 300,
+                      "l2": "points %.1f GB > 129 MB L2" % (flat.nbytes / 1e9), "parallelism": "single"},
+           "clocks": clk, "e2e": None, "gpu_launches": None,
+           "time_to_converge_s": batch_s, "plain_sequential_s": plain_s * scale,
+           "plain_timed_instances": len(sel), "speedup_vs_plain": plain_s * scale / batch_s,
+           "same_results_as_plain": bool(same), "iters_total": int(iters.sum()), "iters_max": int(iters.max()),
+           "converged": int(r["converged"].sum()), "autotune": {"tile_points": tile, "threads": thr,
+                                                                "candidates_ms": info["tune_ms"], "tune_s": tune_s},
+           "flagged": info["flagged"], "fp64_decided": info["fp64_decided"], "generate_s": gen_s}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload.startswith("batch"):
+        return run_batch(args, ws, rank, local)
     return run_ours(args, ws, rank, local)
 
 

@@ -191,6 +191,76 @@ km_status km_lloyd_step_noalloc(const float* x, int64_t ld, int64_t n, int32_t d
 const char* km_last_error(const km_ctx* ctx);
 void km_destroy(km_ctx* ctx);
 
+/* ---- Batched instances ------------------------------------------------
+ * Many independent clustering problems (instance i: N_i points of dimension
+ * d_i in 1..3, K_i in 1..64 clusters) run by shared launches: each step is
+ * one persistent assign kernel over the tiles of every active instance and
+ * one update kernel with a block per instance (section "The Lloyd's
+ * algorithm", steps 2-3, per instance; every instance keeps its own stop
+ * test).  Results per instance are those of km_run on that instance alone:
+ * exact labels, exact fixed-point sums, the same E.
+ *
+ * Layouts (all concatenated in instance order):
+ *   points     instance i is d_i x N_i SoA (row stride N_i) at element
+ *              offset sum_{j<i} d_j N_j;
+ *   labels     N_i int32 at offset sum_{j<i} N_j;
+ *   centroids  K_i x d_i row-major doubles at offset sum_{j<i} K_j d_j;
+ *   counts     K_i int64 at offset sum_{j<i} K_j. */
+typedef struct km_batch km_batch;
+
+/* count instances with sizes n[i], d[i], k[i] (host arrays).  opt may be
+ * NULL; e_mode, tie_rel, use_graph and stream apply.  On a non-OK status
+ * *out may still hold a batch that only km_batch_last_error and
+ * km_batch_destroy accept.
+ * Errors: KM_EINVAL (count < 1, d not in 1..3, K not in 1..64, K > N,
+ *         N >= 2^31), KM_ECUDA. */
+km_status km_batch_create(km_batch** out, int32_t count, const int64_t* n, const int32_t* d, const int32_t* k,
+                          const km_options* opt);
+
+/* Copy all instances' points (layout above; mem KM_HOST or KM_DEVICE_COPY),
+ * then per instance on the GPU: coordinate range, FP32 shift, fixed-point
+ * grid.  Errors: KM_ENUMERIC (NaN/Inf or |x| >= 2^99). */
+km_status km_batch_set_points(km_batch* b, const float* x, int32_t mem);
+
+/* Starting centroids of every instance (host doubles, layout above); resets
+ * every instance's iteration count.  Errors: KM_ENUMERIC (non-finite). */
+km_status km_batch_set_init(km_batch* b, const double* mu0);
+
+/* Time the assign kernel's tile sizes (512, 1024 points) and block sizes
+ * (128, 256, 512 threads) on this batch and keep the fastest (the first
+ * km_batch_run does this when it was not called).  Leaves centroids and
+ * iteration counts unchanged.  Outputs may be NULL. */
+km_status km_batch_tune(km_batch* b, int32_t* tile_out, int32_t* threads_out);
+
+/* Run every instance until its selected error is < tol or max_iter more
+ * steps have run; the steps are replayed from a captured CUDA graph (4 steps
+ * per launch; stopped instances do no work) until no instance is active.
+ * Outputs (host or device pointers, each may be NULL): labels_out (sum N_i),
+ * centroids_out (sum K_i d_i), and per instance iters_out (steps since
+ * km_batch_set_init), e_out (E, or E^2 when e_mode = 1), converged_out.
+ * Returns KM_OK when every instance converged, else KM_NOT_CONVERGED. */
+km_status km_batch_run(km_batch* b, int32_t max_iter, double tol, int32_t* labels_out, double* centroids_out,
+                       int32_t* iters_out, double* e_out, int32_t* converged_out);
+
+/* Cluster sizes of the last step (sum K_i int64, host or device). */
+km_status km_batch_get_counts(km_batch* b, int64_t* counts_out);
+
+typedef struct km_batch_info {
+  int64_t flagged;        /* points re-checked past the FP32 screen, all steps so far */
+  int64_t fp64_decided;   /* of those, decided in FP64 */
+  int32_t tile_points;    /* launch shape in use */
+  int32_t threads;
+  int32_t grid;
+  int32_t tiles;
+  int32_t tuned;          /* 1 once km_batch_tune ran */
+  int32_t tune_candidates;
+  float tune_ms[8];       /* per candidate (tile-major: 512 x {128,256,512}, then 1024 x ...) */
+} km_batch_info;
+km_status km_batch_get_info(km_batch* b, km_batch_info* out);
+
+const char* km_batch_last_error(const km_batch* b);
+void km_batch_destroy(km_batch* b);
+
 /* Library version string and the sm architecture it was built for. */
 const char* km_version(void);
 

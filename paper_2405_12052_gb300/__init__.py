@@ -17,7 +17,7 @@ import re
 
 import numpy as np
 
-__all__ = ["KMeans", "KMError", "lib", "header_symbols", "build", "LIB_PATH", "HEADER"]
+__all__ = ["KMeans", "KMeansBatch", "KMError", "lib", "header_symbols", "build", "LIB_PATH", "HEADER"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libkm.so")
@@ -47,6 +47,13 @@ class _Stats(ctypes.Structure):
                 ("e2", ctypes.c_double), ("flagged", ctypes.c_int64),
                 ("fp64_decided", ctypes.c_int64), ("empty_clusters", ctypes.c_int32),
                 ("overflowed", ctypes.c_int64), ("path", ctypes.c_int32)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("flagged", ctypes.c_int64), ("fp64_decided", ctypes.c_int64), ("tile_points", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("grid", ctypes.c_int32), ("tiles", ctypes.c_int32),
+                ("tuned", ctypes.c_int32), ("tune_candidates", ctypes.c_int32),
+                ("tune_ms", ctypes.c_float * 8)]
 
 
 _lib = None
@@ -109,6 +116,24 @@ def lib(path: str | None = None):
     L.km_last_error.restype = ctypes.c_char_p
     L.km_destroy.argtypes = [P]
     L.km_destroy.restype = None
+    L.km_batch_create.argtypes = [ctypes.POINTER(P), i32, P, P, P, ctypes.POINTER(_Options)]
+    L.km_batch_create.restype = st
+    L.km_batch_set_points.argtypes = [P, P, i32]
+    L.km_batch_set_points.restype = st
+    L.km_batch_set_init.argtypes = [P, P]
+    L.km_batch_set_init.restype = st
+    L.km_batch_tune.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.km_batch_tune.restype = st
+    L.km_batch_run.argtypes = [P, i32, f64, P, P, P, P, P]
+    L.km_batch_run.restype = st
+    L.km_batch_get_counts.argtypes = [P, P]
+    L.km_batch_get_counts.restype = st
+    L.km_batch_get_info.argtypes = [P, ctypes.POINTER(_BatchInfo)]
+    L.km_batch_get_info.restype = st
+    L.km_batch_last_error.argtypes = [P]
+    L.km_batch_last_error.restype = ctypes.c_char_p
+    L.km_batch_destroy.argtypes = [P]
+    L.km_batch_destroy.restype = None
     if path is None:
         _lib = L
     return L
@@ -290,3 +315,121 @@ class KMeans:
         self._check(self._L.km_device_buffers(self._h, ctypes.byref(pts), ctypes.byref(ld),
                                               ctypes.byref(lab), ctypes.byref(mu)))
         return dict(points=pts.value, ld=ld.value, labels=lab.value, centroids=mu.value)
+
+
+class KMeansBatch:
+    """Many independent clustering problems (instance i: N_i points of
+    dimension d_i in 1..3, K_i clusters in 1..64) run by shared launches."""
+
+    def __init__(self, n, d, k, *, e_mode: str = "norm", tie_rel: float = 1e-5, use_graph: bool = True,
+                 stream=None):
+        self._L = lib()
+        self.n = np.ascontiguousarray(n, dtype=np.int64)
+        self.d = np.ascontiguousarray(d, dtype=np.int32)
+        self.k = np.ascontiguousarray(k, dtype=np.int32)
+        self.count = len(self.n)
+        if not (len(self.d) == len(self.k) == self.count):
+            raise ValueError("n, d and k must have one entry per instance")
+        self.x_off = np.concatenate([[0], np.cumsum(self.n * self.d)]).astype(np.int64)
+        self.lab_off = np.concatenate([[0], np.cumsum(self.n)]).astype(np.int64)
+        self.mu_off = np.concatenate([[0], np.cumsum(self.k.astype(np.int64) * self.d)]).astype(np.int64)
+        self.k_off = np.concatenate([[0], np.cumsum(self.k.astype(np.int64))]).astype(np.int64)
+        opt = _Options()
+        self._L.km_default_options(ctypes.byref(opt))
+        opt.e_mode = E_MODES[e_mode]
+        opt.use_graph = 1 if use_graph else 0
+        opt.tie_rel = float(tie_rel)
+        opt.stream = _current_stream() if stream is None else ctypes.c_void_p(
+            stream if isinstance(stream, int) else getattr(stream, "cuda_stream", stream))
+        h = ctypes.c_void_p()
+        s = self._L.km_batch_create(ctypes.byref(h), self.count, self.n.ctypes.data, self.d.ctypes.data,
+                                    self.k.ctypes.data, ctypes.byref(opt))
+        self._h = h
+        self._check(s)
+
+    def _check(self, s: int) -> int:
+        if s < 0:
+            msg = self._L.km_batch_last_error(self._h).decode() if self._h else ""
+            raise KMError(s, msg)
+        return s
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.km_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_points(self, xs):
+        """xs: a list of (d_i, N_i) float32 arrays, or one flat float32 array
+        (numpy, or a CUDA torch tensor) in the concatenated layout."""
+        if isinstance(xs, (list, tuple)):
+            flat = np.concatenate([np.ascontiguousarray(x, dtype=np.float32).reshape(-1) for x in xs])
+        else:
+            flat = xs
+        if _is_torch(flat):
+            if flat.numel() != int(self.x_off[-1]):
+                raise ValueError("flat points of the wrong size")
+            mem = KM_DEVICE_COPY if flat.is_cuda else KM_HOST
+            ptr = flat.data_ptr()
+        else:
+            flat = np.ascontiguousarray(flat, dtype=np.float32)
+            if flat.size != int(self.x_off[-1]):
+                raise ValueError("flat points of the wrong size")
+            mem, ptr = KM_HOST, flat.ctypes.data
+        self._check(self._L.km_batch_set_points(self._h, ptr, mem))
+
+    def set_init(self, mus):
+        """mus: a list of (K_i, d_i) arrays or the flat concatenation."""
+        if isinstance(mus, (list, tuple)):
+            flat = np.concatenate([np.asarray(m, dtype=np.float64).reshape(-1) for m in mus])
+        else:
+            flat = np.asarray(mus, dtype=np.float64).reshape(-1)
+        flat = np.ascontiguousarray(flat)
+        if flat.size != int(self.mu_off[-1]):
+            raise ValueError("flat centroids of the wrong size")
+        self._check(self._L.km_batch_set_init(self._h, flat.ctypes.data))
+
+    def tune(self) -> tuple[int, int]:
+        t, th = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._L.km_batch_tune(self._h, ctypes.byref(t), ctypes.byref(th)))
+        return t.value, th.value
+
+    def run(self, max_iter: int, tol: float, want_labels: bool = True) -> dict:
+        labels = np.empty(int(self.lab_off[-1]), dtype=np.int32) if want_labels else None
+        mu = np.empty(int(self.mu_off[-1]), dtype=np.float64)
+        its = np.empty(self.count, dtype=np.int32)
+        es = np.empty(self.count, dtype=np.float64)
+        conv = np.empty(self.count, dtype=np.int32)
+        s = self._check(self._L.km_batch_run(self._h, int(max_iter), float(tol),
+                                             labels.ctypes.data if want_labels else None, mu.ctypes.data,
+                                             its.ctypes.data, es.ctypes.data, conv.ctypes.data))
+        return dict(labels=labels, centroids=mu, iters=its, E=es, converged=conv.astype(bool),
+                    all_converged=(s == KM_OK))
+
+    def counts(self) -> np.ndarray:
+        out = np.empty(int(self.k_off[-1]), dtype=np.int64)
+        self._check(self._L.km_batch_get_counts(self._h, out.ctypes.data))
+        return out
+
+    def info(self) -> dict:
+        s = _BatchInfo()
+        self._check(self._L.km_batch_get_info(self._h, ctypes.byref(s)))
+        out = {f: getattr(s, f) for f, _ in _BatchInfo._fields_ if f != "tune_ms"}
+        out["tune_ms"] = [float(s.tune_ms[q]) for q in range(s.tune_candidates)]
+        return out
+
+    # per-instance views of flat results
+    def split_labels(self, flat):
+        return [flat[self.lab_off[i]:self.lab_off[i + 1]] for i in range(self.count)]
+
+    def split_centroids(self, flat):
+        return [flat[self.mu_off[i]:self.mu_off[i + 1]].reshape(int(self.k[i]), int(self.d[i]))
+                for i in range(self.count)]
+
+    def split_counts(self, flat):
+        return [flat[self.k_off[i]:self.k_off[i + 1]] for i in range(self.count)]

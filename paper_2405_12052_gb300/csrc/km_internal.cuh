@@ -196,6 +196,55 @@ int64_t gemm_xb_rows(int64_t n);
 int64_t msort_max_chunks(int64_t n, int k);
 cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st);
 
+// ---- batched instances (d <= 3, K <= 64) ----
+constexpr int kBatchMaxK = 64;
+constexpr int kBatchMaxD = 3;
+constexpr int kBatchMaxTile = 1024;  // points per tile: keeps every limb sum in int32
+
+struct BatchInst {        // per instance, written at set_points (scan kernel) and create
+  int64_t n, x_off, lab_off;       // points; element offset of row 0 (rows of n); label offset
+  int32_t d, k, mu_off, k_off;     // mu/ctil offset (K*d), counts offset (K)
+  int32_t tile0, ntiles;           // the instance's tiles (contiguous in the tile list)
+  float s[3];                      // shift (FP32 midrange)
+  float A_max;                     // max fl32 ||x - s||^2
+  int32_t G0;                      // fixed-point grid exponent
+  float C_hi, C_lo;
+  uint32_t bits_C_hi, bits_C_lo;
+};
+
+struct BatchState {       // per instance, advanced on the device
+  int32_t done, iter, converged, empty;
+  int32_t max_iter, pad;
+  double E, E2;
+  float B_max, pad2;
+};
+
+struct BatchArgs {
+  const float* x;
+  const BatchInst* inst;
+  BatchState* state;
+  const int4* tiles;              // {instance, first point, points, 0}
+  const int64_t* tile_poff;       // partial row offset of each tile (K_i (d_i + 1) entries)
+  int ntiles;
+  long long* partials;
+  int32_t* labels;
+  double* mu;
+  float* ctil;
+  long long* counts;
+  unsigned long long* flagged;
+  unsigned long long* fp64;
+  int* active;                    // instances not yet stopped
+  float tau;
+  int e_mode;
+  double tol;
+};
+
+cudaError_t launch_batch_scan(const float* x, BatchInst* inst, int count, unsigned long long* bad, cudaStream_t st);
+cudaError_t launch_batch_tables(const BatchArgs& a, int count, cudaStream_t st);
+cudaError_t launch_batch_assign(const BatchArgs& a, int grid, int threads, cudaStream_t st);
+cudaError_t launch_batch_update(const BatchArgs& a, int count, cudaStream_t st);
+int batch_blocks_per_sm(int threads);
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_assign_fast(int d, int grid, size_t smem, cudaStream_t st, const FastArgs& a);
 size_t fast_smem_bytes(int d, int kpad, int k);

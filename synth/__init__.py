@@ -148,6 +148,32 @@ def init_kmeanspp(x: np.ndarray, k: int, seed: int = 1, sample: int | None = 1 <
     return x[:, idx].T.astype(np.float64), idx
 
 
+def batch_sizes(count: int, seed: int = 0, n_lo: int = 1_000, n_hi: int = 1_000_000,
+                d_choices=(2, 3), k_lo: int = 4, k_hi: int = 64):
+    """Sizes of the batched workload: N_i log-uniform in [n_lo, n_hi], d_i
+    uniform over ``d_choices``, K_i uniform in [k_lo, k_hi] (at most N_i)."""
+    rng = _rng(seed)
+    ns = np.maximum(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count)).astype(np.int64), 1)
+    ds = rng.choice(np.asarray(d_choices), count).astype(np.int64)
+    ks = np.minimum(rng.integers(k_lo, k_hi + 1, count), ns)
+    return ns, ds, ks
+
+
+def batch_instance(i: int, n: int, d: int, k: int, box: float = 10.0, sigma: float = 1.0) -> dict:
+    """Instance i of the batched workload: an isotropic mixture of K
+    Gaussians (sigma, means U[-box, box]^d, equal weights, data seed
+    1000 + i) and K seeded distinct points as the start (seed 2000 + i)."""
+    x, _, _ = iso_mixture(int(n), int(d), int(k), sigma=sigma, box=box, seed=1000 + i, weights="equal")
+    mu0, _ = init_distinct(x, int(k), seed=2000 + i)
+    return dict(x=x, mu0=mu0, n=int(n), d=int(d), k=int(k))
+
+
+def batch_instances(count: int, seed: int = 0, **kw) -> list:
+    """The batched workload (see batch_sizes and batch_instance)."""
+    ns, ds, ks = batch_sizes(count, seed, **kw)
+    return [batch_instance(i, ns[i], ds[i], ks[i]) for i in range(count)]
+
+
 # Named workloads.  Each returns dict(x, mu0, k, tol, max_iter, name, desc).
 def _c1(scale=1.0):
     n = int(100_000 * scale)
