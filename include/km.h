@@ -101,6 +101,20 @@ km_status km_set_points(km_ctx* ctx, const float* x, int64_t ld, int32_t layout,
  * Errors: KM_EINVAL (null), KM_ENUMERIC (non-finite). */
 km_status km_set_init(km_ctx* ctx, const double* mu0);
 
+/* k-means++ seeding (D^2 sampling, Arthur and Vassilvitskii 2007) on the
+ * context's points, then km_set_init with the result.  u: K uniforms in
+ * [0, 1) (host), the only randomness: the first centre is point
+ * floor(u[0] N); centre c is the first point whose running sum of D^2
+ * (squared FP64 distance to the nearest centre chosen so far, coordinates in
+ * order) exceeds u[c] times the total, the last point if none does.  The
+ * sums run over 4096-point chunks in a fixed order, so the picks equal a
+ * sequential scan's except when a target lies within FP64 rounding of a
+ * running-sum boundary.  Outputs (host, may be NULL): mu_out K x d doubles,
+ * idx_out K point indices.  Needs km_set_points first; d <= 256; allocates
+ * N + N/4096 + 4096 doubles of scratch for the call.
+ * Errors: KM_ESTATE, KM_EINVAL (u outside [0, 1)), KM_ENOMEM, KM_ECUDA. */
+km_status km_init_kmeanspp(km_ctx* ctx, const double* u, double* mu_out, int64_t* idx_out);
+
 /* One Lloyd step from the current centroids: reassignment, mean update and
  * error.  Writes E (sqrt of E^2) and E^2 to the non-NULL outputs and
  * synchronizes the stream.  Errors: KM_ESTATE, KM_ECUDA. */

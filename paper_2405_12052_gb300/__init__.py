@@ -116,6 +116,8 @@ def lib(path: str | None = None):
     L.km_last_error.restype = ctypes.c_char_p
     L.km_destroy.argtypes = [P]
     L.km_destroy.restype = None
+    L.km_init_kmeanspp.argtypes = [P, P, P, P]
+    L.km_init_kmeanspp.restype = st
     L.km_batch_create.argtypes = [ctypes.POINTER(P), i32, P, P, P, ctypes.POINTER(_Options)]
     L.km_batch_create.restype = st
     L.km_batch_set_points.argtypes = [P, P, i32]
@@ -245,6 +247,17 @@ class KMeans:
     def set_init(self, mu0):
         mu0 = np.ascontiguousarray(np.asarray(mu0, dtype=np.float64).reshape(self.k, self.d))
         self._check(self._L.km_set_init(self._h, mu0.ctypes.data))
+
+    def init_kmeanspp(self, u):
+        """k-means++ seeding on the GPU with the K uniforms ``u`` in [0, 1);
+        sets the starting centroids and returns (mu0 (K, d), indices)."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        if u.shape != (self.k,):
+            raise ValueError("need K uniforms")
+        mu = np.empty((self.k, self.d), dtype=np.float64)
+        idx = np.empty(self.k, dtype=np.int64)
+        self._check(self._L.km_init_kmeanspp(self._h, u.ctypes.data, mu.ctypes.data, idx.ctypes.data))
+        return mu, idx
 
     def step(self):
         e, e2 = ctypes.c_double(), ctypes.c_double()

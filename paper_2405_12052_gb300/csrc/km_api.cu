@@ -447,6 +447,43 @@ km_status km_set_init(km_ctx* c, const double* mu0) {
   return KM_OK;
 }
 
+km_status km_init_kmeanspp(km_ctx* c, const double* u, double* mu_out, int64_t* idx_out) {
+  if (!c) return KM_EINVAL;
+  if (!u) return fail(c, KM_EINVAL, "null uniforms");
+  if (!c->have_points) return fail(c, KM_ESTATE, "km_init_kmeanspp before km_set_points");
+  if (c->d > kMaxKppD) return fail(c, KM_EINVAL, "d > 256 for k-means++");
+  for (int q = 0; q < c->k; ++q)
+    if (!(u[q] >= 0.0 && u[q] < 1.0)) return fail(c, KM_EINVAL, "uniforms must lie in [0, 1)");
+  const int64_t n = c->n;
+  const int64_t nch = kpp_chunks(n);
+  double *du = nullptr, *dmu = nullptr, *d2 = nullptr, *cs = nullptr, *sc = nullptr;
+  int64_t* didx = nullptr;
+  auto release = [&]() {
+    void* b[] = {du, dmu, d2, cs, sc, didx};
+    for (void* p : b)
+      if (p) cudaFree(p);
+  };
+  cudaError_t e = cudaSuccess;
+  if ((e = dalloc(&du, (size_t)c->k)) != cudaSuccess || (e = dalloc(&dmu, (size_t)c->k * c->d)) != cudaSuccess ||
+      (e = dalloc(&d2, (size_t)n)) != cudaSuccess || (e = dalloc(&cs, (size_t)nch)) != cudaSuccess ||
+      (e = dalloc(&sc, (size_t)4096)) != cudaSuccess || (e = dalloc(&didx, (size_t)c->k)) != cudaSuccess) {
+    release();
+    return fail(c, KM_ENOMEM, std::string("k-means++ buffers: ") + cudaGetErrorString(e));
+  }
+  std::vector<double> hmu((size_t)c->k * c->d);
+  std::vector<int64_t> hidx((size_t)c->k);
+  e = cudaMemcpyAsync(du, u, sizeof(double) * c->k, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = launch_kmeanspp(c->x, c->ld, n, c->d, c->k, du, dmu, didx, d2, cs, sc, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hmu.data(), dmu, sizeof(double) * hmu.size(), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hidx.data(), didx, sizeof(int64_t) * hidx.size(), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  release();
+  if (e != cudaSuccess) return fail(c, KM_ECUDA, std::string("k-means++: ") + cudaGetErrorString(e));
+  if (mu_out) std::memcpy(mu_out, hmu.data(), sizeof(double) * hmu.size());
+  if (idx_out) std::memcpy(idx_out, hidx.data(), sizeof(int64_t) * hidx.size());
+  return km_set_init(c, hmu.data());
+}
+
 km_status km_step(km_ctx* c, double* e_out, double* e2_out) {
   km_status s = ready(c);
   if (s != KM_OK) return s;

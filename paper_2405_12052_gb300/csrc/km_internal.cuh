@@ -245,6 +245,12 @@ cudaError_t launch_batch_assign(const BatchArgs& a, int grid, int threads, cudaS
 cudaError_t launch_batch_update(const BatchArgs& a, int count, cudaStream_t st);
 int batch_blocks_per_sm(int threads);
 
+// ---- k-means++ seeding ----
+constexpr int kMaxKppD = 256;
+int64_t kpp_chunks(int64_t n);
+cudaError_t launch_kmeanspp(const float* x, int64_t ld, int64_t n, int d, int k, const double* u, double* mu,
+                            int64_t* idx, double* d2, double* chunk_sum, double* scan, cudaStream_t st);
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_assign_fast(int d, int grid, size_t smem, cudaStream_t st, const FastArgs& a);
 size_t fast_smem_bytes(int d, int kpad, int k);
