@@ -275,6 +275,57 @@ km_status km_batch_get_info(km_batch* b, km_batch_info* out);
 const char* km_batch_last_error(const km_batch* b);
 void km_batch_destroy(km_batch* b);
 
+/* ---- Learned initialiser ------------------------------------------------
+ * A set network that predicts K starting centres from a sample of S points
+ * (the paper notes how the result depends on the initial centres, section
+ * "The Lloyd's algorithm"): per point h1 = relu(W1 x' + b1) and
+ * h2 = relu(W2 h1 + b2) (128 wide) on x' = (x - m) / s, the sample's
+ * per-coordinate mean m and population std s (1 where 0); g = the mean of h2
+ * over the points; a3 = relu(W3 g + b3); p = W4 a3 + b4 (K x d); centres
+ * c = p * s + m.  Training minimises the mean over sets of the symmetric
+ * Chamfer distance between p and the standardised target centres.
+ * Parameters are one float32 vector in the order W1 (128 x d), b1, W2
+ * (128 x 128), b2, W3 (128 x 128), b3, W4 (K d x 128), b4 (row-major).
+ * Inputs: x is [B][S][d] float32 (set b, point i, coordinate j at
+ * (b S + i) d + j), targets [B][K][d]; S a positive multiple of 64; mem
+ * KM_HOST (copied) or a device kind (the pointer is read in place).  FP32
+ * kernels, every sum in a fixed order: a step is deterministic. */
+typedef struct km_setnet km_setnet;
+
+/* d in 1..3, K in 1..64; parameters start at zero (set them).  stream may be
+ * NULL (the network creates one). */
+km_status km_setnet_create(km_setnet** out, int32_t d, int32_t k, void* stream);
+int64_t km_setnet_param_count(const km_setnet* net);
+int32_t km_setnet_dims(const km_setnet* net, int32_t* k_out); /* returns d */
+void* km_setnet_stream(const km_setnet* net);
+/* Host copies of the parameters; setting them also clears Adam's moments. */
+km_status km_setnet_set_params(km_setnet* net, const float* params);
+km_status km_setnet_get_params(km_setnet* net, float* params_out);
+/* Forward, loss and backward on a batch of B sets; the gradients stay on the
+ * device (km_setnet_get_grads copies them).  loss_out (host) may be NULL
+ * (then nothing synchronizes). */
+km_status km_setnet_loss_grad(km_setnet* net, const float* x, const float* targets, int32_t B, int32_t S,
+                              int32_t mem, float* loss_out);
+km_status km_setnet_get_grads(km_setnet* net, float* grads_out);
+/* One Adam step (Kingma and Ba 2015, bias-corrected) with the last gradients. */
+km_status km_setnet_adam(km_setnet* net, float lr, float beta1, float beta2, float eps);
+/* loss_grad + Adam (beta1 0.9, beta2 0.999, eps 1e-8). */
+km_status km_setnet_train_step(km_setnet* net, const float* x, const float* targets, int32_t B, int32_t S,
+                               int32_t mem, float lr, float* loss_out);
+/* Centres for each of B sets: centroids_out [B][K][d] doubles (host or device). */
+km_status km_setnet_predict(km_setnet* net, const float* x, int32_t B, int32_t S, int32_t mem,
+                            double* centroids_out);
+const char* km_setnet_last_error(const km_setnet* net);
+void km_setnet_destroy(km_setnet* net);
+
+/* Starting centroids of a context from the network: a sample of sample_n
+ * points (a positive multiple of 64) of the context's points, point
+ * floor(u_j N) for u_j the j-th SplitMix64 output from seed (53 bits), then
+ * km_setnet_predict and km_set_init.  mu_out (host K x d) may be NULL.
+ * Errors: KM_ESTATE (no points), KM_EINVAL (d or K differ from the
+ * network's), KM_ENOMEM, KM_ECUDA. */
+km_status km_init_learned(km_ctx* ctx, km_setnet* net, int32_t sample_n, uint64_t seed, double* mu_out);
+
 /* Library version string and the sm architecture it was built for. */
 const char* km_version(void);
 

@@ -17,7 +17,7 @@ import re
 
 import numpy as np
 
-__all__ = ["KMeans", "KMeansBatch", "KMError", "lib", "header_symbols", "build", "LIB_PATH", "HEADER"]
+__all__ = ["KMeans", "KMeansBatch", "SetNet", "KMError", "lib", "header_symbols", "build", "LIB_PATH", "HEADER"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libkm.so")
@@ -118,6 +118,34 @@ def lib(path: str | None = None):
     L.km_destroy.restype = None
     L.km_init_kmeanspp.argtypes = [P, P, P, P]
     L.km_init_kmeanspp.restype = st
+    L.km_setnet_create.argtypes = [ctypes.POINTER(P), i32, i32, P]
+    L.km_setnet_create.restype = st
+    L.km_setnet_param_count.argtypes = [P]
+    L.km_setnet_param_count.restype = i64
+    L.km_setnet_dims.argtypes = [P, ctypes.POINTER(i32)]
+    L.km_setnet_dims.restype = i32
+    L.km_setnet_stream.argtypes = [P]
+    L.km_setnet_stream.restype = P
+    L.km_setnet_set_params.argtypes = [P, P]
+    L.km_setnet_set_params.restype = st
+    L.km_setnet_get_params.argtypes = [P, P]
+    L.km_setnet_get_params.restype = st
+    L.km_setnet_get_grads.argtypes = [P, P]
+    L.km_setnet_get_grads.restype = st
+    L.km_setnet_loss_grad.argtypes = [P, P, P, i32, i32, i32, ctypes.POINTER(ctypes.c_float)]
+    L.km_setnet_loss_grad.restype = st
+    L.km_setnet_adam.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    L.km_setnet_adam.restype = st
+    L.km_setnet_train_step.argtypes = [P, P, P, i32, i32, i32, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]
+    L.km_setnet_train_step.restype = st
+    L.km_setnet_predict.argtypes = [P, P, i32, i32, i32, P]
+    L.km_setnet_predict.restype = st
+    L.km_setnet_last_error.argtypes = [P]
+    L.km_setnet_last_error.restype = ctypes.c_char_p
+    L.km_setnet_destroy.argtypes = [P]
+    L.km_setnet_destroy.restype = None
+    L.km_init_learned.argtypes = [P, P, i32, ctypes.c_uint64, P]
+    L.km_init_learned.restype = st
     L.km_batch_create.argtypes = [ctypes.POINTER(P), i32, P, P, P, ctypes.POINTER(_Options)]
     L.km_batch_create.restype = st
     L.km_batch_set_points.argtypes = [P, P, i32]
@@ -258,6 +286,14 @@ class KMeans:
         idx = np.empty(self.k, dtype=np.int64)
         self._check(self._L.km_init_kmeanspp(self._h, u.ctypes.data, mu.ctypes.data, idx.ctypes.data))
         return mu, idx
+
+    def init_learned(self, net: "SetNet", sample_n: int = 4096, seed: int = 0):
+        """Starting centroids from the set network on a seeded sample of
+        ``sample_n`` points; sets them and returns them (K, d)."""
+        mu = np.empty((self.k, self.d), dtype=np.float64)
+        self._check(self._L.km_init_learned(self._h, net._h, int(sample_n), int(seed) & (2**64 - 1),
+                                            mu.ctypes.data))
+        return mu
 
     def step(self):
         e, e2 = ctypes.c_double(), ctypes.c_double()
@@ -446,3 +482,91 @@ class KMeansBatch:
 
     def split_counts(self, flat):
         return [flat[self.k_off[i]:self.k_off[i + 1]] for i in range(self.count)]
+
+
+class SetNet:
+    """The learned initialiser's set network (d in 1..3, K in 1..64)."""
+
+    def __init__(self, d: int, k: int, stream=None):
+        self._L = lib()
+        self.d, self.k = int(d), int(k)
+        h = ctypes.c_void_p()
+        st = _current_stream() if stream is None else ctypes.c_void_p(
+            stream if isinstance(stream, int) else getattr(stream, "cuda_stream", stream))
+        s = self._L.km_setnet_create(ctypes.byref(h), self.d, self.k, st)
+        self._h = h
+        self._check(s)
+        self.nparam = int(self._L.km_setnet_param_count(self._h))
+
+    def _check(self, s: int) -> int:
+        if s < 0:
+            msg = self._L.km_setnet_last_error(self._h).decode() if self._h else ""
+            raise KMError(s, msg)
+        return s
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.km_setnet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arr(self, a, shape_tail):
+        """(pointer, mem kind, keep-alive) of points [B][S][d] or targets."""
+        if _is_torch(a):
+            import torch
+            if a.dtype != torch.float32:
+                raise TypeError("float32 tensors only")
+            a = a.contiguous()
+            return a.data_ptr(), (KM_DEVICE_BORROW if a.is_cuda else KM_HOST), a
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        return a.ctypes.data, KM_HOST, a
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32).reshape(-1)
+        if flat.size != self.nparam:
+            raise ValueError(f"need {self.nparam} parameters")
+        self._check(self._L.km_setnet_set_params(self._h, flat.ctypes.data))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.nparam, dtype=np.float32)
+        self._check(self._L.km_setnet_get_params(self._h, out.ctypes.data))
+        return out
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(self.nparam, dtype=np.float32)
+        self._check(self._L.km_setnet_get_grads(self._h, out.ctypes.data))
+        return out
+
+    def loss_grad(self, x, t) -> float:
+        B, S = int(x.shape[0]), int(x.shape[1])
+        px, mx, kx = self._arr(x, None)
+        pt, mt, kt = self._arr(t, None)
+        if mx != mt:
+            raise ValueError("points and targets must live in the same memory")
+        loss = ctypes.c_float()
+        self._check(self._L.km_setnet_loss_grad(self._h, px, pt, B, S, mx, ctypes.byref(loss)))
+        return float(loss.value)
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        self._check(self._L.km_setnet_adam(self._h, lr, beta1, beta2, eps))
+
+    def train_step(self, x, t, lr: float, want_loss: bool = True):
+        B, S = int(x.shape[0]), int(x.shape[1])
+        px, mx, kx = self._arr(x, None)
+        pt, mt, kt = self._arr(t, None)
+        loss = ctypes.c_float()
+        self._check(self._L.km_setnet_train_step(self._h, px, pt, B, S, mx, float(lr),
+                                                 ctypes.byref(loss) if want_loss else None))
+        return float(loss.value) if want_loss else None
+
+    def predict(self, x) -> np.ndarray:
+        B, S = int(x.shape[0]), int(x.shape[1])
+        px, mx, kx = self._arr(x, None)
+        out = np.empty((B, self.k, self.d), dtype=np.float64)
+        self._check(self._L.km_setnet_predict(self._h, px, B, S, mx, out.ctypes.data))
+        return out

@@ -484,6 +484,31 @@ km_status km_init_kmeanspp(km_ctx* c, const double* u, double* mu_out, int64_t* 
   return km_set_init(c, hmu.data());
 }
 
+km_status km_init_learned(km_ctx* c, km_setnet* net, int32_t sample_n, uint64_t seed, double* mu_out) {
+  if (!c) return KM_EINVAL;
+  if (!net) return fail(c, KM_EINVAL, "null network");
+  if (!c->have_points) return fail(c, KM_ESTATE, "km_init_learned before km_set_points");
+  int32_t nk = 0;
+  const int32_t nd = km_setnet_dims(net, &nk);
+  if (nd != c->d || nk != c->k) return fail(c, KM_EINVAL, "network d or K differs from the context's");
+  if (sample_n < 64 || sample_n % 64) return fail(c, KM_EINVAL, "sample_n must be a positive multiple of 64");
+  float* buf = nullptr;
+  cudaError_t e = dalloc(&buf, (size_t)sample_n * c->d);
+  if (e != cudaSuccess) return fail(c, KM_ENOMEM, std::string("sample buffer: ") + cudaGetErrorString(e));
+  e = launch_setnet_sample(c->x, c->ld, c->n, c->d, sample_n, (unsigned long long)seed, buf, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // the network runs on its own stream
+  if (e != cudaSuccess) {
+    cudaFree(buf);
+    return fail(c, KM_ECUDA, std::string("sample: ") + cudaGetErrorString(e));
+  }
+  std::vector<double> mu((size_t)c->k * c->d);
+  const km_status s = km_setnet_predict(net, buf, 1, sample_n, KM_DEVICE_BORROW, mu.data());
+  cudaFree(buf);
+  if (s != KM_OK) return fail(c, s, std::string("network: ") + km_setnet_last_error(net));
+  if (mu_out) std::memcpy(mu_out, mu.data(), sizeof(double) * mu.size());
+  return km_set_init(c, mu.data());
+}
+
 km_status km_step(km_ctx* c, double* e_out, double* e2_out) {
   km_status s = ready(c);
   if (s != KM_OK) return s;

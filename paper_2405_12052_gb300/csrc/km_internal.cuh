@@ -251,6 +251,30 @@ int64_t kpp_chunks(int64_t n);
 cudaError_t launch_kmeanspp(const float* x, int64_t ld, int64_t n, int d, int k, const double* u, double* mu,
                             int64_t* idx, double* d2, double* chunk_sum, double* scan, cudaStream_t st);
 
+// ---- learned initialiser: set network (d <= 3, K <= 64, H = 128) ----
+constexpr int kSetH = 128;
+struct SetNetArgs {
+  const float* x;     // [B][S][d] points
+  const float* t;     // [B][K][d] targets (training)
+  int B, S, d, k;
+  const float* prm;   // flat parameters
+  float* grads;
+  float* xs; float* ts; float* ms;   // standardised points, targets; [B][2d] mean, std
+  float* w2t; float* h1; float* h2; float* tile_pool; float* G; float* P; float* dG; float* loss;
+  float* dz2; float* dz1; float* part;
+};
+int setnet_param_count(int d, int k);
+size_t setnet_point_smem();
+int64_t setnet_part_floats(int64_t P, int d);
+cudaError_t launch_setnet_forward(const SetNetArgs& a, bool train, cudaStream_t st);
+cudaError_t launch_setnet_backward(const SetNetArgs& a, cudaStream_t st);
+cudaError_t launch_setnet_adam(float* prm, const float* grads, float* m, float* v, int n, float lr, float b1,
+                               float b2, float eps, float c1, float c2, cudaStream_t st);
+cudaError_t launch_setnet_sample(const float* x, int64_t ld, int64_t n, int d, int S, unsigned long long seed,
+                                 float* out, cudaStream_t st);
+cudaError_t launch_setnet_destandardize(const float* P, const float* ms, int B, int d, int k, double* out,
+                                        cudaStream_t st);
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_assign_fast(int d, int grid, size_t smem, cudaStream_t st, const FastArgs& a);
 size_t fast_smem_bytes(int d, int kpad, int k);
