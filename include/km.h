@@ -147,6 +147,12 @@ km_status km_sync(km_ctx* ctx, int32_t* iters_out, double* e_out, int32_t* done_
 /* The stream the context queues its work on (a cudaStream_t). */
 void* km_stream(km_ctx* ctx);
 
+/* The objective sum_i ||x_i - mu_{z_i}||^2 of the current labels (last step)
+ * and centroids, in FP64 with the oracle's order: per point coordinates in
+ * order, points in index order within 65536-point chunks, then the chunks
+ * in order.  Synchronizes.  Errors: KM_ESTATE, KM_ENOMEM, KM_ECUDA. */
+km_status km_objective(km_ctx* ctx, double* obj_out);
+
 /* Copy results of the last step.  mem: KM_HOST or KM_DEVICE_COPY (device
  * pointer of the caller).  Sizes: labels N int32, centroids K x d doubles,
  * counts K int64.  Synchronize the stream. */

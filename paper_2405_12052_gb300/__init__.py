@@ -144,6 +144,8 @@ def lib(path: str | None = None):
     L.km_setnet_last_error.restype = ctypes.c_char_p
     L.km_setnet_destroy.argtypes = [P]
     L.km_setnet_destroy.restype = None
+    L.km_objective.argtypes = [P, ctypes.POINTER(f64)]
+    L.km_objective.restype = st
     L.km_init_learned.argtypes = [P, P, i32, ctypes.c_uint64, P]
     L.km_init_learned.restype = st
     L.km_batch_create.argtypes = [ctypes.POINTER(P), i32, P, P, P, ctypes.POINTER(_Options)]
@@ -286,6 +288,13 @@ class KMeans:
         idx = np.empty(self.k, dtype=np.int64)
         self._check(self._L.km_init_kmeanspp(self._h, u.ctypes.data, mu.ctypes.data, idx.ctypes.data))
         return mu, idx
+
+    def objective(self) -> float:
+        """sum_i ||x_i - mu_{z_i}||^2 of the last step's labels and the
+        current centroids (FP64, the oracle's summation order)."""
+        o = ctypes.c_double()
+        self._check(self._L.km_objective(self._h, ctypes.byref(o)))
+        return o.value
 
     def init_learned(self, net: "SetNet", sample_n: int = 4096, seed: int = 0):
         """Starting centroids from the set network on a seeded sample of

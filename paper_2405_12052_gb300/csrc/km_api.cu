@@ -47,6 +47,7 @@ struct km_ctx {
   float* scan = nullptr;  // [2d] min/max + [1] amax
   unsigned long long* scan_bad = nullptr;
   size_t fast_smem = 0;
+  int nwin = 2;  // fused path: sum windows per warp
   int path = 0;  // 1 fused (d <= 4, K <= 256), 2 generic, 3 tensor cores (d = 64, K <= 1024)
   // tensor-core path
   void* xb = nullptr;
@@ -166,6 +167,7 @@ cudaError_t launch_assign(km_ctx* c) {
     a.tab2 = c->tab2; a.ctil = c->ctil4; a.mu = c->mu; a.ic = c->ic; a.dc = c->dc;
     a.ls = c->ls; a.labels = c->labels; a.partials = c->partials;
     a.ntiles = (c->n + kWarpTile - 1) / kWarpTile;
+    a.nwin = c->nwin;
     e = launch_assign_fast(c->d, c->G, c->fast_smem, c->st, a);
   } else {
     GenericArgs a{};
@@ -265,7 +267,13 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
   const bool gemm = d == kGemmD && k <= kGemmMaxK && n < (int64_t(1) << 31) &&
                     gemm_smem_bytes((k + 255) / 256 * 256) <= (size_t)p.sharedMemPerBlockOptin;
   if (c->fast) {
-    c->fast_smem = fast_smem_bytes(d, c->kpad, k);
+    // one 32-bit sum window per half-warp when it fits, else one per warp
+    c->nwin = 2;
+    c->fast_smem = fast_smem_bytes(d, c->kpad, k, 2);
+    if (c->fast_smem > (size_t)p.sharedMemPerBlockOptin) {
+      c->nwin = 1;
+      c->fast_smem = fast_smem_bytes(d, c->kpad, k, 1);
+    }
     if (c->fast_smem > (size_t)p.sharedMemPerBlockOptin) c->fast = false;
   }
   const int64_t ntiles = (n + kWarpTile - 1) / kWarpTile;  // warp-tiles of 256 points
@@ -507,6 +515,22 @@ km_status km_init_learned(km_ctx* c, km_setnet* net, int32_t sample_n, uint64_t 
   if (s != KM_OK) return fail(c, s, std::string("network: ") + km_setnet_last_error(net));
   if (mu_out) std::memcpy(mu_out, mu.data(), sizeof(double) * mu.size());
   return km_set_init(c, mu.data());
+}
+
+km_status km_objective(km_ctx* c, double* obj_out) {
+  km_status s = ready(c);
+  if (s != KM_OK) return s;
+  if (!obj_out) return fail(c, KM_EINVAL, "null output");
+  double* part = nullptr;
+  const int64_t nch = objective_chunks(c->n);
+  cudaError_t e = dalloc(&part, (size_t)nch + 1);
+  if (e != cudaSuccess) return fail(c, KM_ENOMEM, std::string("objective buffer: ") + cudaGetErrorString(e));
+  e = launch_objective(c->x, c->ld, c->n, c->d, c->mu, c->labels, part, part + nch, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(obj_out, part + nch, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  cudaFree(part);
+  if (e != cudaSuccess) return fail(c, KM_ECUDA, std::string("objective: ") + cudaGetErrorString(e));
+  return KM_OK;
 }
 
 km_status km_step(km_ctx* c, double* e_out, double* e2_out) {

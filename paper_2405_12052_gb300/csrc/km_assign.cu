@@ -195,9 +195,9 @@ struct FastSmem {
   float4* gtab;             // [kpad/4][GS] screen table by group: slot j = coefficient j of the 4 centroids
   float* xbuf;              // [kWarps][2][D][kWarpTile] double-buffered points
   uint32_t* queue;          // [kWarps][kWarpQueue] flagged points
-  uint32_t* win;            // [kWarps][2][k+1][WIN] 32-bit windows per half-warp; bin k discards
+  uint32_t* win;            // [kWarps][nwin][k+1][WIN] 32-bit windows (per half-warp when nwin = 2); bin k discards
   int* cnt;                 // [2]: flagged, fp64-decided (block totals)
-  __device__ FastSmem(unsigned char* sm, int kpad, int k) {
+  __device__ FastSmem(unsigned char* sm, int kpad, int k, int nwin) {
     tab = reinterpret_cast<unsigned long long*>(sm);
     acc = reinterpret_cast<long long*>(tab + (size_t)kpad * DP);
     ctil = reinterpret_cast<float4*>(acc + (size_t)kWarps * k * DP);
@@ -205,16 +205,16 @@ struct FastSmem {
     xbuf = reinterpret_cast<float*>(gtab + (size_t)(kpad / 4) * GS);
     queue = reinterpret_cast<uint32_t*>(xbuf + (size_t)kWarps * 2 * D * kWarpTile);
     win = queue + (size_t)kWarps * kWarpQueue;
-    cnt = reinterpret_cast<int*>(win + (size_t)kWarps * 2 * (k + 1) * WIN);
+    cnt = reinterpret_cast<int*>(win + (size_t)kWarps * nwin * (k + 1) * WIN);
   }
 };
 
-// Flush both half-warp windows of a warp into its int64 totals.  acc
+// Flush the warp's windows (nwin of them) into its int64 totals.  acc
 // columns per centroid: 0..D-1 coordinate sums, D the count (the layout of
 // the per-block partials); window slots: 0 the count, 1..D the high limbs,
 // D+1..2D the low limbs.
 template <int D>
-__device__ __forceinline__ void flush_windows(uint32_t* wwarp, long long* acc, int k, int lane,
+__device__ __forceinline__ void flush_windows(uint32_t* wwarp, long long* acc, int k, int nwin, int lane,
                                               uint32_t bias_hi, uint32_t bias_lo) {
   constexpr int DP = D + 1, WIN = 2 * D + 1;
   const int half = (k + 1) * WIN;
@@ -222,8 +222,7 @@ __device__ __forceinline__ void flush_windows(uint32_t* wwarp, long long* acc, i
   for (int s = lane; s < k * DP; s += 32) {
     const int kk = s / DP, j = s - kk * DP;
     long long v = 0;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < nwin; ++h) {
       const uint32_t* w = wwarp + h * half + kk * WIN;
       const uint32_t c = w[0];
       if (j == D) {
@@ -237,7 +236,7 @@ __device__ __forceinline__ void flush_windows(uint32_t* wwarp, long long* acc, i
     acc[s] += v;
   }
   __syncwarp();
-  for (int s = lane; s < 2 * half; s += 32) wwarp[s] = 0u;
+  for (int s = lane; s < nwin * half; s += 32) wwarp[s] = 0u;
   __syncwarp();
 }
 
@@ -263,12 +262,14 @@ __device__ __forceinline__ void prefetch_tile(const FastArgs& a, float* xb, int6
 }
 
 // Re-decide the points in this warp's queue (warp-level: lanes take
-// entries; windows are flushed every 32 rounds, <= 512 additions per bin).
+// entries; windows are flushed every 32 rounds with two windows per warp, 16
+// with one: <= 512 additions per bin).
 template <int D>
 __device__ void drain_warp_queue(const FastArgs& a, FastSmem<D>& sm, uint32_t* q, int qn, int wid,
                                  int wtot, uint32_t* wwarp, uint32_t* wmine, long long* acc, int lane,
                                  const float* s, const DataConst& dc, float B_max, float tau, int& n64) {
-  flush_windows<D>(wwarp, acc, a.k, lane, dc.bits_C_hi, dc.bits_C_lo);
+  flush_windows<D>(wwarp, acc, a.k, a.nwin, lane, dc.bits_C_hi, dc.bits_C_lo);
+  const int rmask = a.nwin == 2 ? 31 : 15;
   for (int r = 0, b = 0; b < qn; ++r, b += 32) {
     const int e = b + lane;
     if (e < qn) {
@@ -284,9 +285,9 @@ __device__ void drain_warp_queue(const FastArgs& a, FastSmem<D>& sm, uint32_t* q
       a.labels[i] = kk;
       accumulate_point<D>(wmine, kk, xo, dc.C_hi, dc.C_lo);
     }
-    if ((r & 31) == 31) flush_windows<D>(wwarp, acc, a.k, lane, dc.bits_C_hi, dc.bits_C_lo);
+    if ((r & rmask) == rmask) flush_windows<D>(wwarp, acc, a.k, a.nwin, lane, dc.bits_C_hi, dc.bits_C_lo);
   }
-  flush_windows<D>(wwarp, acc, a.k, lane, dc.bits_C_hi, dc.bits_C_lo);
+  flush_windows<D>(wwarp, acc, a.k, a.nwin, lane, dc.bits_C_hi, dc.bits_C_lo);
 }
 
 // Per-launch constants of the fused kernel, in registers.
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
   constexpr int DP = D + 1, WIN = 2 * D + 1, GS = FastSmem<D>::GS;
   extern __shared__ __align__(16) unsigned char smraw[];
   if (a.ls->done) return;  // the loop already stopped (graph-driven runs)
-  FastSmem<D> sm(smraw, a.kpad, a.k);
+  FastSmem<D> sm(smraw, a.kpad, a.k, a.nwin);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = a.k, kpad = a.kpad;
 
@@ -490,8 +491,9 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
 #pragma unroll
   for (int j = 0; j < D; ++j) { s[j] = dc.s[j]; s2[j] = dup2(dc.s[j]); }
 
-  uint32_t* wwarp = sm.win + (size_t)warp * 2 * (k + 1) * WIN;
-  uint32_t* wmine = wwarp + (size_t)(lane >> 4) * (k + 1) * WIN;
+  const int nwin = a.nwin;
+  uint32_t* wwarp = sm.win + (size_t)warp * nwin * (k + 1) * WIN;
+  uint32_t* wmine = wwarp + (size_t)(nwin == 2 ? (lane >> 4) : 0) * (k + 1) * WIN;
   long long* acc = sm.acc + (size_t)warp * k * DP;
   uint32_t* q = sm.queue + (size_t)warp * kWarpQueue;
   float* xb = sm.xbuf + (size_t)warp * 2 * D * kWarpTile;
@@ -508,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
   }
   for (int q2 = tid; q2 < k; q2 += kThreads) sm.ctil[q2] = a.ctil[q2];
   for (int q2 = tid; q2 < kWarps * k * DP; q2 += kThreads) sm.acc[q2] = 0;
-  for (int q2 = tid; q2 < kWarps * 2 * (k + 1) * WIN; q2 += kThreads) sm.win[q2] = 0u;
+  for (int q2 = tid; q2 < kWarps * nwin * (k + 1) * WIN; q2 += kThreads) sm.win[q2] = 0u;
   if (tid < 2) sm.cnt[tid] = 0;
   __syncthreads();
 
@@ -530,8 +532,9 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
       process_tile<D, true>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
     else
       process_tile<D, false>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
-    if (++since_flush == 4) {  // 16 lanes x 8 points x 4 tiles: <= 512 additions per half-warp bin
-      flush_windows<D>(wwarp, acc, k, lane, dc.bits_C_hi, dc.bits_C_lo);
+    // 16 lanes x 8 points x 4 tiles (or 32 lanes x 8 points x 2 tiles): <= 512 additions per bin
+    if (++since_flush == (nwin == 2 ? 4 : 2)) {
+      flush_windows<D>(wwarp, acc, k, nwin, lane, dc.bits_C_hi, dc.bits_C_lo);
       since_flush = 0;
     }
     if (qn > kWarpQueue - kWarpTile) {
@@ -548,7 +551,7 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
     drain_warp_queue<D>(a, sm, q, qn, wid, wtot, wwarp, wmine, acc, lane, s, dc, ic.B_max, ic.tau, n64);
     nflag += qn;
   } else {
-    flush_windows<D>(wwarp, acc, k, lane, dc.bits_C_hi, dc.bits_C_lo);
+    flush_windows<D>(wwarp, acc, k, nwin, lane, dc.bits_C_hi, dc.bits_C_lo);
   }
   if (lane == 0 && nflag) atomicAdd(&sm.cnt[0], nflag);
   if (n64) atomicAdd(&sm.cnt[1], n64);
@@ -641,11 +644,11 @@ __global__ void __launch_bounds__(kThreads) assign_generic_kernel(GenericArgs a)
 
 }  // namespace
 
-size_t fast_smem_bytes(int d, int kpad, int k) {
+size_t fast_smem_bytes(int d, int kpad, int k, int nwin) {
   const int dp = d + 1, win = 2 * d + 1, gs = (dp & 1) ? dp : dp + 1;
   size_t b = (size_t)kpad * dp * 8 + (size_t)kWarps * k * dp * 8 + (size_t)k * 16 + (size_t)(kpad / 4) * gs * 16 +
              (size_t)kWarps * 2 * d * kWarpTile * 4 + (size_t)kWarps * kWarpQueue * 4 +
-             (size_t)kWarps * 2 * (k + 1) * win * 4 + 16;
+             (size_t)kWarps * nwin * (k + 1) * win * 4 + 16;
   return (b + 15) & ~size_t(15);
 }
 

@@ -111,6 +111,7 @@ struct FastArgs {
   int32_t* labels;
   long long* partials;             // [gridDim.x][k][D+1]
   int64_t ntiles;
+  int nwin;                        // 32-bit sum windows per warp: 2 (one per half-warp) or 1 (large K)
 };
 
 struct GenericArgs {
@@ -275,9 +276,14 @@ cudaError_t launch_setnet_sample(const float* x, int64_t ld, int64_t n, int d, i
 cudaError_t launch_setnet_destandardize(const float* P, const float* ms, int B, int d, int k, double* out,
                                         cudaStream_t st);
 
+// ---- objective ----
+int64_t objective_chunks(int64_t n);
+cudaError_t launch_objective(const float* x, int64_t ld, int64_t n, int d, const double* mu, const int32_t* z,
+                             double* part, double* out, cudaStream_t st);
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_assign_fast(int d, int grid, size_t smem, cudaStream_t st, const FastArgs& a);
-size_t fast_smem_bytes(int d, int kpad, int k);
+size_t fast_smem_bytes(int d, int kpad, int k, int nwin);
 int fast_blocks_per_sm(int d, size_t smem);
 cudaError_t launch_assign_generic(int grid, size_t smem, cudaStream_t st, const GenericArgs& a);
 size_t generic_smem_bytes(int d, int k);

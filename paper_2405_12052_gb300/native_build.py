@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libkm.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["km_assign.cu", "km_update.cu", "km_api.cu", "km_noalloc.cu", "km_gemm.cu", "km_msort.cu",
            "km_batch.cu", "km_batch_api.cu", "km_kpp.cu",
-           "km_setnet.cu", "km_setnet_api.cu"]
+           "km_setnet.cu", "km_setnet_api.cu", "km_objective.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-Xptxas", "-v"]

@@ -35,6 +35,9 @@ def test_kmeanspp_matches_oracle(km, oracle, n, d, k, seed):
     r = g.run(5, 0.0)
     ref = oracle.run(x, mu_ref, 5, 0.0)
     assert np.array_equal(r["labels"], ref["labels"])
+    # the objective of the final labels and centres, in the oracle's order
+    # (the centres agree to within their own rounding)
+    assert abs(g.objective() - ref["objective"]) <= 1e-12 * ref["objective"]
     g.close()
 
 
