@@ -131,26 +131,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def source_hash():
+KERNEL_SOURCES = {
+    "assign_fast_kernel<3>": ("km_assign.cu", "km_internal.cuh"),
+    "gemm_assign_kernel": ("km_gemm.cu", "km_internal.cuh"),
+}
+
+
+def source_hash(files=("km_assign.cu", "km_internal.cuh")):
     h = hashlib.sha256()
-    for f in ("km_assign.cu", "km_internal.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2405_12052_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload, n, k, d):
-    """DRAM bytes per launch of the assign kernel from the committed ncu
-    summary, if it was taken on the current source (else None)."""
-    p = os.path.join(ROOT, "profiles", "assign_fast_traffic.json")
-    if not os.path.exists(p):
+def profiled_traffic(kernel, n, k, d):
+    """DRAM bytes per launch of a kernel from the committed ncu summaries
+    (profiles/traffic.json), if taken on the current source of that kernel
+    and the same d and K (else None).  A capture on a smaller N is scaled by
+    the points streamed (the traffic grows in proportion)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
         return None
-    rec = json.load(open(p))
-    if rec.get("source_sha") != source_hash():
-        return None
-    if rec.get("d") != d or rec.get("k") != k:
-        return None
-    # captured on a smaller N: traffic grows in proportion to the points streamed
-    return rec["dram_bytes_per_launch"] * (n / rec["n"])
+    for rec in json.load(open(p)):
+        if rec.get("kernel") != kernel or rec.get("d") != d or rec.get("k") != k:
+            continue
+        if rec.get("source_sha") != source_hash(KERNEL_SOURCES[kernel]):
+            continue
+        return rec["dram_bytes_per_launch"] * (n / rec["n"])
+    return None
 
 
 def cpu_baseline(w, seconds):
@@ -312,7 +320,7 @@ def run_ours(args, ws, rank, local):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     flops = 3.0 * n * k * d  # the algorithmic count: d subtractions, squares and adds per pair
     achieved = flops / (assign_ms / 1e3) / 1e12
-    traffic = profiled_traffic(args.workload, n, k, d)
+    traffic = profiled_traffic("gemm_assign_kernel" if stats["path"] == 3 else f"assign_fast_kernel<{d}>", n, k, d)
     if stats["path"] == 3:
         # the contraction x.c: 2*N*K*d flops per launch (multiply-adds of the
         # BF16 GEMM); the norms and the screen epilogue are not counted
