@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batch workloads")
+    ap.add_argument("--learned-count", type=int, default=6, help="held-out mixtures of the learned-init workload")
     ap.add_argument("--plain-every", type=int, default=1,
                     help="batch workloads: time plain km_run on every m-th instance (scaled up)")
     return ap.parse_args()
@@ -457,6 +458,55 @@ def run_batch(args, ws, rank, local):
     return 0
 
 
+def run_learned(args, ws, rank, local):
+    """Learned initialiser against k-means++ on held-out N = 1e7 anisotropic
+    mixtures (K = 16): iterations to tol 1e-6, wall time (start + Lloyd) and
+    final objective of each; the learned result counts only when its
+    objective is within 1e-6 relative of the k-means++ result's (else the
+    fallback's cost is added)."""
+    import numpy as np
+    import synth
+    count = args.learned_count
+    n = args.n or 10_000_000
+    xs = [synth.aniso_mixture(n, 3, 16, seed=900 + s)[0] for s in range(count)]
+    import torch
+    import paper_2405_12052_gb300 as km
+    from paper_2405_12052_gb300 import learned
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    km.build()
+    net = learned.load()
+    rows = []
+    for s, x in enumerate(xs):
+        g = km.KMeans(n, 3, 16)
+        g.set_points(torch.from_numpy(x).cuda(), borrow=True)
+        u = np.random.default_rng(700 + s).random(16)
+        for _ in range(2):  # the second pass is the timed one (first builds graphs)
+            r = learned.run_with_fallback(g, net, u, seed=s)
+        rows.append(r)
+        g.close()
+    ok = [r["objective_learned"] <= r["objective_kpp"] * (1 + 1e-6) for r in rows]
+    wall_l = sum(r["wall_learned"] + (0.0 if o else r["wall_kpp"]) for r, o in zip(rows, ok))
+    wall_k = sum(r["wall_kpp"] for r in rows)
+    it_l = [r["iters_learned"] for r in rows]
+    it_k = [r["iters_kpp"] for r in rows]
+    evals = n * 16 * sum(it_l)
+    out = {"metric": METRIC, "value": evals / sum(r["wall_learned"] for r in rows), "unit": UNIT, "n_gpus": 1,
+           "steps": int(sum(it_l)), "warmup": 1, "ms_per_step": 1e3 * sum(r["wall_learned"] for r in rows) / max(1, sum(it_l)),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"learned_init_3d_n{n}_k16", "mixtures": count, "sample": 4096,
+                      "init": "set network vs k-means++ (uniforms seed 700 + s)", "tol": 1e-6, "max_iter": 300,
+                      "parallelism": "single"},
+           "clocks": None, "e2e": None, "gpu_launches": None,
+           "iters_learned": it_l, "iters_kpp": it_k,
+           "objective_ratio_learned_over_kpp": [r["objective_learned"] / r["objective_kpp"] for r in rows],
+           "learned_within_1e-6": int(sum(ok)), "wall_learned_with_fallback_s": wall_l, "wall_kpp_s": wall_k,
+           "speedup_vs_kpp": wall_k / wall_l}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -464,6 +514,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.workload.startswith("batch"):
         return run_batch(args, ws, rank, local)
+    if args.workload.startswith("learned"):
+        return run_learned(args, ws, rank, local)
     return run_ours(args, ws, rank, local)
 
 

@@ -1,0 +1,65 @@
+"""What the trained set network gains, and what the fallback guarantees.
+
+* Training on the GPU kernels lowers the held-out Chamfer loss.
+* The committed network (trained on 200,000 mixtures) has a lower held-out
+  loss than the untrained one.
+* Learned start + Lloyd with the k-means++ judge never ends with an
+  objective above the k-means++ result's (beyond 1e-6 relative); the
+  iterations and objectives of both starts are printed."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def km():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2405_12052_gb300 as m
+    m.build()
+    return m
+
+
+def test_training_lowers_the_held_out_loss(km):
+    from paper_2405_12052_gb300 import learned
+    x, means = learned.mixtures(2048 + 64, S=1024, seed=77)
+    t, _ = learned.converged_targets(x, means)
+    xv, tv = x[2048:].contiguous(), t[2048:].contiguous()
+    net0 = km.SetNet(3, 16)
+    net0.set_params(learned.init_params(3, 16, seed=0))
+    l0 = net0.loss_grad(xv, tv)
+    net, hist = learned.train(x[:2048], t[:2048], epochs=4, batch=32, lr=2e-3, log_every=10_000, log=lambda s: None)
+    l1 = net.loss_grad(xv, tv)
+    assert l1 < 0.8 * l0, (l0, l1)
+
+
+def test_committed_network_and_fallback(km, oracle):
+    from paper_2405_12052_gb300 import learned
+    if not os.path.exists(learned.WEIGHTS):
+        pytest.skip("no committed weights")
+    net = learned.load()
+    x, means = learned.mixtures(256, seed=31337)
+    t, _ = learned.converged_targets(x, means)
+    untrained = km.SetNet(3, 16)
+    untrained.set_params(learned.init_params(3, 16, seed=0))
+    assert net.loss_grad(x, t) < 0.7 * untrained.loss_grad(x, t)
+    report = []
+    for s in range(3):
+        xs = synth.aniso_mixture(200_000, 3, 16, seed=950 + s)[0]
+        g = km.KMeans(200_000, 3, 16)
+        g.set_points(xs)
+        u = np.random.default_rng(s).random(16)
+        r = learned.run_with_fallback(g, net, u, seed=s)
+        kept = min(r["objective_learned"], r["objective_kpp"]) if r["used"] == "learned" else r["objective_kpp"]
+        assert kept <= r["objective_kpp"] * (1 + 1e-6)
+        assert (r["used"] == "learned") == (r["objective_learned"] <= r["objective_kpp"] * (1 + 1e-6))
+        report.append({k: v for k, v in r.items() if k != "centroids"})
+        g.close()
+    print(json.dumps(report))
