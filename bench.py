@@ -54,6 +54,20 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank gets it)."""
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(n, k, steps, ws, total_ms):
+    """Point-centroid evaluations of all ranks' replicas per second of the
+    slowest rank's timed region."""
+    return n * k * steps * ws / (total_ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -286,11 +300,9 @@ def run_ours(args, ws, rank, local):
     assert st["iters"] == W + K, st
     assign_ms = statistics.mean(ea[i].elapsed_time(eb[i]) for i in range(K))
     if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
     ms_step = total_ms / K
-    value = n * k * K * ws / (total_ms / 1e3)
+    value = whole_job_value(n, k, K, ws, total_ms)
     stats = g.stats()  # of the last timed step
 
     # end to end through the public API with host buffers (pinned)
