@@ -6,11 +6,12 @@
 // Points of all instances are cut into tiles of at most 1024 points listed
 // instance-major.  Per step:
 //  * batch_assign_kernel (persistent: CTAs stride over the tile list): per
-//    tile, the instance's FP32 centroid table in shared memory; per point the
-//    FP32 direct-form distances to all K centres on coordinates shifted by
-//    the instance's shift, the argmin and runner-up, and the rigorous bound
-//    that sends an unresolved point to FP64 in the oracle's order (lowest
-//    index on ties); then exact fixed-point sums: each coordinate split into
+//    tile, the instance's screen table in shared memory; per pair of points
+//    the FP32 expanded-form values ||c~||^2 - 2 x~.c~ to all K centres on
+//    coordinates shifted by the instance's shift (paired FMA chains), the
+//    argmin and runner-up, and the rigorous bound that sends an unresolved
+//    point to FP64 in the oracle's order (lowest index on ties); then exact
+//    fixed-point sums: each coordinate split into
 //    two 32-bit limbs added with 32-bit shared atomics (a tile of <= 1024
 //    points keeps every limb sum inside int32), written as one int64 partial
 //    row per (tile, cluster) plus the count.
@@ -65,70 +66,112 @@ __device__ __forceinline__ double i128_to_double(unsigned long long lo, long lon
   return neg ? -r : r;
 }
 
-// The points of one tile (d = D): labels and the fixed-point limb sums.
+__device__ __forceinline__ unsigned long long bfma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long bpack(float lo, float hi) {
+  unsigned long long p;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(p) : "f"(lo), "f"(hi));
+  return p;
+}
+__device__ __forceinline__ void bunpack(unsigned long long p, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+// running minimum and runner-up with the minimum's index (first index on
+// equal values)
+__device__ __forceinline__ void btop2(float& b, float& s, int& i, float v, int c) {
+  const bool lt = v < b;
+  s = lt ? b : fminf(s, v);
+  i = lt ? c : i;
+  b = lt ? v : b;
+}
+
+// The points of one tile (d = D), two per thread per round: screen values
+// v_k = n'_k + sum_j x~_j (-2 c~_kj) (= ||c~_k||^2 - 2 x~.c~_k) by one paired
+// FMA chain per centroid from the duplicated table w2 ({(-2c~_j, -2c~_j)},
+// (n'_k, n'_k)); a point is decided when its two smallest values are apart by
+// more than their rigorous error (FMA chains, n'_k's rounding, the rounding
+// of x~ and c~, the oracle's FP64 error) plus 1e-5 D; otherwise in FP64 in
+// the oracle's order.  Then labels and the fixed-point limb sums.
 template <int D>
-__device__ __forceinline__ void tile_points(const BatchArgs& a, const BatchInst& bi, const float* s_c, int* s_acc,
-                                            int start, int count, float B_max, int& myflag, int& my64) {
+__device__ __forceinline__ void tile_points(const BatchArgs& a, const BatchInst& bi,
+                                            const unsigned long long* __restrict__ w2, int* s_acc, int start,
+                                            int count, float B_max, int& myflag, int& my64) {
   const int k = bi.k;
   constexpr int W = 2 * D + 1;
   const float sB = sqrtf(B_max);
-  for (int p = threadIdx.x; p < count; p += blockDim.x) {
-    const int64_t i = (int64_t)start + p;
-    float xo[D], xt[D];
-    float A = 0.f;
+  const int step = blockDim.x;
+  for (int p = threadIdx.x; p < count; p += 2 * step) {
+    const bool two = p + step < count;
+    float xo[2][D], A[2] = {0.f, 0.f};
+    unsigned long long X[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      xo[j] = a.x[bi.x_off + (int64_t)j * bi.n + i];
-      xt[j] = __fsub_rn(xo[j], bi.s[j]);
-      A = __fmaf_rn(xt[j], xt[j], A);
+      const float* row = a.x + bi.x_off + (int64_t)j * bi.n + start;
+      xo[0][j] = row[p];
+      xo[1][j] = two ? row[p + step] : xo[0][j];
+      const float t0 = __fsub_rn(xo[0][j], bi.s[j]), t1 = __fsub_rn(xo[1][j], bi.s[j]);
+      A[0] = __fmaf_rn(t0, t0, A[0]);
+      A[1] = __fmaf_rn(t1, t1, A[1]);
+      X[j] = bpack(t0, t1);
     }
-    A *= 1.0001f;
-    float best = 3.0e38f, second = 3.0e38f;
-    int kb = 0;
+    float b[2] = {3.0e38f, 3.0e38f}, sv[2] = {3.0e38f, 3.0e38f};
+    int ib[2] = {0, 0};
     for (int c = 0; c < k; ++c) {
-      float dv = 0.f;
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        const float u = __fsub_rn(xt[j], s_c[c * D + j]);
-        dv = __fmaf_rn(u, u, dv);
-      }
-      if (dv < best) { second = best; best = dv; kb = c; }
-      else if (dv < second) { second = dv; }
+      const ulonglong2 wa = *reinterpret_cast<const ulonglong2*>(w2 + 4 * c);
+      const ulonglong2 wb = *reinterpret_cast<const ulonglong2*>(w2 + 4 * c + 2);
+      unsigned long long r = bfma2(X[0], wa.x, wb.y);
+      if constexpr (D > 1) r = bfma2(X[1], wa.y, r);
+      if constexpr (D > 2) r = bfma2(X[2], wb.x, r);
+      float v0, v1;
+      bunpack(r, v0, v1);
+      btop2(b[0], sv[0], ib[0], v0, c);
+      btop2(b[1], sv[1], ib[1], v1, c);
     }
-    if (k > 1) {
-      const float sA = sqrtf(A), AB = A + B_max;
-      const float e1 = bbound(best, sA, sB, AB, D), e2 = bbound(second, sA, sB, AB, D);
-      const float lo2 = second - e2, hi1 = best + e1;
-      if (!((lo2 > hi1) && (lo2 - hi1 > a.tau * (second + e2)))) {
-        ++myflag;
-        ++my64;
-        const double* mu = a.mu + bi.mu_off;
-        double bd = bd64(xo, mu, D);
-        kb = 0;
-        for (int c = 1; c < k; ++c) {
-          const double dd = bd64(xo, mu + c * D, D);
-          if (dd < bd) { bd = dd; kb = c; }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      if (e == 1 && !two) break;
+      const int64_t i = (int64_t)start + p + e * step;
+      int kb = ib[e];
+      if (k > 1) {
+        const float Ae = A[e] * 1.0001f, sA = sqrtf(Ae);
+        const float ev = 2.03f * (float)(D + 1) * kBU * (B_max + 2.f * sA * sB);  // one value's chain error
+        const float thr = 2.f * ev + 4.001f * kBU * (Ae + 2.f * B_max) +
+                          2.f * kBU64x * (float)(D + 1) * (Ae + B_max) + a.tau * (sv[e] + Ae + ev) + 1e-30f;
+        if (!(sv[e] - b[e] > thr)) {
+          ++myflag;
+          ++my64;
+          const double* mu = a.mu + bi.mu_off;
+          double bd = bd64(xo[e], mu, D);
+          kb = 0;
+          for (int c = 1; c < k; ++c) {
+            const double dd = bd64(xo[e], mu + c * D, D);
+            if (dd < bd) { bd = dd; kb = c; }
+          }
         }
       }
-    }
-    a.labels[bi.lab_off + i] = kb;
-    int* acc = s_acc + kb * W;
-    atomicAdd(&acc[0], 1);
+      a.labels[bi.lab_off + i] = kb;
+      int* acc = s_acc + kb * W;
+      atomicAdd(&acc[0], 1);
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-      // exact split on the instance's fixed-point grid (unit 2^G0)
-      const float tt = __fadd_rn(xo[j], bi.C_hi);
-      const float h = __fsub_rn(tt, bi.C_hi);
-      const float r = __fsub_rn(xo[j], h);
-      const float t2 = __fadd_rn(r, bi.C_lo);
-      atomicAdd(&acc[1 + j], (int)(__float_as_uint(tt) - bi.bits_C_hi));
-      atomicAdd(&acc[1 + D + j], (int)(__float_as_uint(t2) - bi.bits_C_lo));
+      for (int j = 0; j < D; ++j) {
+        // exact split on the instance's fixed-point grid (unit 2^G0)
+        const float tt = __fadd_rn(xo[e][j], bi.C_hi);
+        const float h = __fsub_rn(tt, bi.C_hi);
+        const float r = __fsub_rn(xo[e][j], h);
+        const float t2 = __fadd_rn(r, bi.C_lo);
+        atomicAdd(&acc[1 + j], (int)(__float_as_uint(tt) - bi.bits_C_hi));
+        atomicAdd(&acc[1 + D + j], (int)(__float_as_uint(t2) - bi.bits_C_lo));
+      }
     }
   }
 }
 
-__global__ void __launch_bounds__(1024) batch_assign_kernel(BatchArgs a) {
-  __shared__ float s_c[kBatchMaxK * 3];      // c~ = fl32(mu - s)
+__global__ void __launch_bounds__(kBatchMaxThreads) batch_assign_kernel(BatchArgs a) {
+  __shared__ __align__(16) unsigned long long s_w2[kBatchMaxK * 4];  // duplicated screen table
   __shared__ int s_acc[kBatchMaxK * 7];      // per cluster: count, hi limbs, lo limbs
   __shared__ int s_nflag, s_n64;
   const int tid = threadIdx.x;
@@ -139,13 +182,24 @@ __global__ void __launch_bounds__(1024) batch_assign_kernel(BatchArgs a) {
     if (a.state[inst].done) continue;  // block-uniform
     const BatchInst bi = a.inst[inst];
     const int d = bi.d, k = bi.k, w = 2 * d + 1;
-    for (int q = tid; q < k * d; q += blockDim.x) s_c[q] = a.ctil[bi.mu_off + q];
+    for (int c = tid; c < k; c += blockDim.x) {
+      float n = 0.f, m[3] = {0.f, 0.f, 0.f};
+      for (int j = 0; j < d; ++j) {
+        const float cv = a.ctil[bi.mu_off + c * d + j];
+        n = __fmaf_rn(cv, cv, n);
+        m[j] = -2.f * cv;  // exact
+      }
+      s_w2[4 * c + 0] = bpack(m[0], m[0]);
+      s_w2[4 * c + 1] = bpack(m[1], m[1]);
+      s_w2[4 * c + 2] = bpack(m[2], m[2]);
+      s_w2[4 * c + 3] = bpack(n, n);
+    }
     for (int q = tid; q < k * w; q += blockDim.x) s_acc[q] = 0;
     __syncthreads();
     const float B_max = a.state[inst].B_max;
-    if (d == 3) tile_points<3>(a, bi, s_c, s_acc, tl.y, tl.z, B_max, myflag, my64);
-    else if (d == 2) tile_points<2>(a, bi, s_c, s_acc, tl.y, tl.z, B_max, myflag, my64);
-    else tile_points<1>(a, bi, s_c, s_acc, tl.y, tl.z, B_max, myflag, my64);
+    if (d == 3) tile_points<3>(a, bi, s_w2, s_acc, tl.y, tl.z, B_max, myflag, my64);
+    else if (d == 2) tile_points<2>(a, bi, s_w2, s_acc, tl.y, tl.z, B_max, myflag, my64);
+    else tile_points<1>(a, bi, s_w2, s_acc, tl.y, tl.z, B_max, myflag, my64);
     __syncthreads();
     long long* prow = a.partials + a.tile_poff[t];
     for (int q = tid; q < k * (d + 1); q += blockDim.x) {

@@ -201,6 +201,7 @@ cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st);
 constexpr int kBatchMaxK = 64;
 constexpr int kBatchMaxD = 3;
 constexpr int kBatchMaxTile = 1024;  // points per tile: keeps every limb sum in int32
+constexpr int kBatchMaxThreads = 512;  // assign block size limit (per-warp windows in shared memory)
 
 struct BatchInst {        // per instance, written at set_points (scan kernel) and create
   int64_t n, x_off, lab_off;       // points; element offset of row 0 (rows of n); label offset
