@@ -64,6 +64,8 @@ typedef enum {
 enum { KM_SOA_DxN = 0, KM_AOS_NxD = 1 };                       /* point layouts */
 enum { KM_HOST = 0, KM_DEVICE_COPY = 1, KM_DEVICE_BORROW = 2 }; /* where a buffer lives */
 enum { KM_E_NORM = 0, KM_E_SQUARED = 1 };                      /* which error km_run tests */
+enum { KM_LABELS_EVERY_STEP = 0, KM_LABELS_FINAL = 1 };         /* label write policy */
+enum { KM_DIST_AUTO = 0, KM_DIST_SIMT = 1, KM_DIST_TENSOR = 2 }; /* distance path */
 
 typedef struct km_options {
   int32_t e_mode;  /* KM_E_NORM (default): stop when sqrt(E^2) < tol;
@@ -72,6 +74,15 @@ typedef struct km_options {
                         with a device-side stop; 0: one host round trip per step */
   double tie_rel;  /* relative near-tie threshold re-decided in FP64 (default 1e-5) */
   void* stream;    /* cudaStream_t for all work (NULL: the context creates one) */
+  int32_t label_policy; /* KM_LABELS_EVERY_STEP (default): every step writes its labels
+                           (the "final cluster indicators" are the last step's);
+                           KM_LABELS_FINAL: steps skip the N label writes and
+                           km_run ends with one assignment pass against the returned
+                           centroids (km_write_labels); ignored by the tensor-core
+                           path, whose next step reads the labels */
+  int32_t dist_path;    /* KM_DIST_AUTO (default): tensor cores for d = 64 and K <= 1024,
+                           else FP32 SIMT; KM_DIST_SIMT: FP32 SIMT kernels always;
+                           KM_DIST_TENSOR: the tcgen05 path or KM_EINVAL */
 } km_options;
 
 /* Fill *opt with the defaults above. */
@@ -146,6 +157,13 @@ km_status km_sync(km_ctx* ctx, int32_t* iters_out, double* e_out, int32_t* done_
 
 /* The stream the context queues its work on (a cudaStream_t). */
 void* km_stream(km_ctx* ctx);
+
+/* Labels of the current centroids: one assignment pass (its sums are not
+ * used; the stop flag does not stop it) writing the N labels, for the
+ * KM_LABELS_FINAL policy (km_run calls it at the end).  Queued on the stream;
+ * km_get_labels synchronizes.  No-op on the tensor-core path (its steps
+ * always write labels).  Errors: KM_ESTATE, KM_ECUDA. */
+km_status km_write_labels(km_ctx* ctx);
 
 /* The objective sum_i ||x_i - mu_{z_i}||^2 of the current labels (last step)
  * and centroids, in FP64 with the oracle's order: per point coordinates in

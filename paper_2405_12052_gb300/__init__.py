@@ -39,7 +39,12 @@ class KMError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("e_mode", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("tie_rel", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("tie_rel", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("label_policy", ctypes.c_int32), ("dist_path", ctypes.c_int32)]
+
+
+LABEL_POLICIES = {"every_step": 0, "final": 1}
+DIST_PATHS = {"auto": 0, "simt": 1, "tensor": 2}
 
 
 class _Stats(ctypes.Structure):
@@ -144,6 +149,8 @@ def lib(path: str | None = None):
     L.km_setnet_last_error.restype = ctypes.c_char_p
     L.km_setnet_destroy.argtypes = [P]
     L.km_setnet_destroy.restype = None
+    L.km_write_labels.argtypes = [P]
+    L.km_write_labels.restype = st
     L.km_objective.argtypes = [P, ctypes.POINTER(f64)]
     L.km_objective.restype = st
     L.km_init_learned.argtypes = [P, P, i32, ctypes.c_uint64, P]
@@ -196,12 +203,15 @@ class KMeans:
     """One clustering problem: N points of dimension d, K clusters."""
 
     def __init__(self, n: int, d: int, k: int, *, e_mode: str = "norm", tie_rel: float = 1e-5,
-                 use_graph: bool = True, stream=None):
+                 use_graph: bool = True, stream=None, label_policy: str = "every_step",
+                 dist_path: str = "auto"):
         self._L = lib()
         self.n, self.d, self.k = int(n), int(d), int(k)
         opt = _Options()
         self._L.km_default_options(ctypes.byref(opt))
         opt.e_mode = E_MODES[e_mode]
+        opt.label_policy = LABEL_POLICIES[label_policy]
+        opt.dist_path = DIST_PATHS[dist_path]
         opt.use_graph = 1 if use_graph else 0
         opt.tie_rel = float(tie_rel)
         if stream is None:
@@ -288,6 +298,11 @@ class KMeans:
         idx = np.empty(self.k, dtype=np.int64)
         self._check(self._L.km_init_kmeanspp(self._h, u.ctypes.data, mu.ctypes.data, idx.ctypes.data))
         return mu, idx
+
+    def write_labels(self):
+        """Labels of the current centroids (one assignment pass; for the
+        "final" label policy)."""
+        self._check(self._L.km_write_labels(self._h))
 
     def objective(self) -> float:
         """sum_i ||x_i - mu_{z_i}||^2 of the last step's labels and the

@@ -150,8 +150,12 @@ cudaError_t launch_tables(km_ctx* c) {
 }
 
 // Reassignment (+ per-block sums on paths 1 and 2), one kernel.
-cudaError_t launch_assign(km_ctx* c) {
+// labels_pass: the final-labels pass of the "final" label policy (writes the
+// labels of the current centroids even after the stop flag; the per-block
+// sums it also forms are not used).
+cudaError_t launch_assign(km_ctx* c, bool labels_pass = false) {
   cudaError_t e;
+  const int store = (c->opt.label_policy == KM_LABELS_EVERY_STEP || labels_pass) ? 1 : 0;
   if (c->path == 3) {
     GemmArgs g{};
     g.xb = c->xb; g.xa = c->xa_pt; g.xaos = c->xaos; g.cb = c->cbf; g.nprime = c->nprime; g.ctil = c->ctil;
@@ -168,6 +172,8 @@ cudaError_t launch_assign(km_ctx* c) {
     a.ls = c->ls; a.labels = c->labels; a.partials = c->partials;
     a.ntiles = (c->n + kWarpTile - 1) / kWarpTile;
     a.nwin = c->nwin;
+    a.store_labels = store;
+    a.ignore_done = labels_pass ? 1 : 0;
     e = launch_assign_fast(c->d, c->G, c->fast_smem, c->st, a);
   } else {
     GenericArgs a{};
@@ -175,6 +181,8 @@ cudaError_t launch_assign(km_ctx* c) {
     a.ctil = c->ctil; a.cnorm = c->cnorm; a.mu = c->mu; a.shift = c->shift; a.dc = c->dc;
     a.ls = c->ls; a.labels = c->labels; a.partials = c->partials;
     a.A_max = c->A_max; a.B_max_ptr = c->gen_bmax; a.tau = (float)(c->opt.tie_rel * (1.0 + 1e-4));
+    a.store_labels = store;
+    a.ignore_done = labels_pass ? 1 : 0;
     e = launch_assign_generic(c->G, 0, c->st, a);
   }
   return e;
@@ -233,6 +241,8 @@ void km_default_options(km_options* opt) {
   opt->use_graph = 1;
   opt->tie_rel = 1e-5;
   opt->stream = nullptr;
+  opt->label_policy = KM_LABELS_EVERY_STEP;
+  opt->dist_path = KM_DIST_AUTO;
 }
 
 const char* km_version(void) { return "libkm 0.1 (sm_103a)"; }
@@ -249,6 +259,10 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
   km_default_options(&c->opt);
   if (opt) c->opt = *opt;
   if (!(c->opt.tie_rel >= 0.0 && c->opt.tie_rel < 0.5)) return fail(c, KM_EINVAL, "tie_rel out of range");
+  if (c->opt.label_policy != KM_LABELS_EVERY_STEP && c->opt.label_policy != KM_LABELS_FINAL)
+    return fail(c, KM_EINVAL, "label_policy out of range");
+  if (c->opt.dist_path < KM_DIST_AUTO || c->opt.dist_path > KM_DIST_TENSOR)
+    return fail(c, KM_EINVAL, "dist_path out of range");
   if (c->opt.e_mode != KM_E_NORM && c->opt.e_mode != KM_E_SQUARED) return fail(c, KM_EINVAL, "bad e_mode");
   KM_CUDA(c, cudaGetDevice(&c->dev));
   cudaDeviceProp p{};
@@ -277,7 +291,9 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
     if (c->fast_smem > (size_t)p.sharedMemPerBlockOptin) c->fast = false;
   }
   const int64_t ntiles = (n + kWarpTile - 1) / kWarpTile;  // warp-tiles of 256 points
-  c->path = c->fast ? 1 : (gemm ? 3 : 2);
+  if (c->opt.dist_path == KM_DIST_TENSOR && !gemm)
+    return fail(c, KM_EINVAL, "tensor-core distances need d = 64, K <= 1024 and N < 2^31");
+  c->path = c->opt.dist_path == KM_DIST_TENSOR ? 3 : (c->fast ? 1 : ((gemm && c->opt.dist_path == KM_DIST_AUTO) ? 3 : 2));
   if (c->path == 3) {
     c->kpad = (k + 255) / 256 * 256;
     c->G = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, c->sms));
@@ -533,6 +549,16 @@ km_status km_objective(km_ctx* c, double* obj_out) {
   return KM_OK;
 }
 
+km_status km_write_labels(km_ctx* c) {
+  km_status s = ready(c);
+  if (s != KM_OK) return s;
+  if (c->path == 3) return KM_OK;  // the tensor-core path writes labels every step
+  KM_CUDA(c, launch_assign(c, true));
+  // the pass's re-check counters are not a step's: clear them
+  KM_CUDA(c, cudaMemsetAsync(&c->ls->flagged, 0, 2 * sizeof(unsigned long long), c->st));
+  return KM_OK;
+}
+
 km_status km_step(km_ctx* c, double* e_out, double* e2_out) {
   km_status s = ready(c);
   if (s != KM_OK) return s;
@@ -584,6 +610,10 @@ km_status km_run(km_ctx* c, int32_t max_iter, double tol, int32_t* labels_out,
         if (c->host_ls.done) break;
       }
     }
+  }
+  if (c->opt.label_policy == KM_LABELS_FINAL) {
+    s = km_write_labels(c);
+    if (s != KM_OK) return s;
   }
   if (labels_out)
     KM_CUDA(c, cudaMemcpyAsync(labels_out, c->labels, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st));

@@ -282,7 +282,7 @@ __device__ void drain_warp_queue(const FastArgs& a, FastSmem<D>& sm, uint32_t* q
       bool used64;
       const int kk = recheck_fast<D>(xo, s, sm.ctil, a.mu, a.k, B_max, tau, used64);
       n64 += used64 ? 1 : 0;
-      a.labels[i] = kk;
+      if (a.store_labels) a.labels[i] = kk;
       accumulate_point<D>(wmine, kk, xo, dc.C_hi, dc.C_lo);
     }
     if ((r & rmask) == rmask) flush_windows<D>(wwarp, acc, a.k, a.nwin, lane, dc.bits_C_hi, dc.bits_C_lo);
@@ -435,6 +435,7 @@ __device__ __forceinline__ void process_tile(const FastArgs& a, FastSmem<D>& sm,
 #pragma unroll
   for (int g = 0; g < kNG; ++g) {
     const int64_t i0 = base + g * kGS + 4 * lane;
+    if (!a.store_labels) break;
     if constexpr (FULL) {
       *reinterpret_cast<int4*>(a.labels + i0) = make_int4(lab[4 * g], lab[4 * g + 1], lab[4 * g + 2], lab[4 * g + 3]);
     } else {
@@ -479,7 +480,7 @@ template <int D>
 __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs a) {
   constexpr int DP = D + 1, WIN = 2 * D + 1, GS = FastSmem<D>::GS;
   extern __shared__ __align__(16) unsigned char smraw[];
-  if (a.ls->done) return;  // the loop already stopped (graph-driven runs)
+  if (a.ls->done && !a.ignore_done) return;  // the loop already stopped (graph-driven runs)
   FastSmem<D> sm(smraw, a.kpad, a.k, a.nwin);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = a.k, kpad = a.kpad;
@@ -575,7 +576,7 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
 // 64-bit atomics into this block's own partial row.
 __global__ void __launch_bounds__(kThreads) assign_generic_kernel(GenericArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  if (a.ls->done) return;
+  if (a.ls->done && !a.ignore_done) return;
   const int d = a.d, k = a.k, dp = d + 1;
   unsigned long long* row = reinterpret_cast<unsigned long long*>(a.partials) + (size_t)blockIdx.x * k * dp;
   for (int q = threadIdx.x; q < k * dp; q += blockDim.x) row[q] = 0ull;
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(kThreads) assign_generic_kernel(GenericArgs a)
         }
       }
     }
-    a.labels[i] = kb;
+    if (a.store_labels) a.labels[i] = kb;
     unsigned long long* r = row + (size_t)kb * dp;
     for (int j = 0; j < d; ++j) {
       uint32_t bh, bl;

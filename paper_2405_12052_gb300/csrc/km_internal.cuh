@@ -112,6 +112,8 @@ struct FastArgs {
   long long* partials;             // [gridDim.x][k][D+1]
   int64_t ntiles;
   int nwin;                        // 32-bit sum windows per warp: 2 (one per half-warp) or 1 (large K)
+  int store_labels;                // 0: labels are not written (label policy "final")
+  int ignore_done;                 // 1: run even after the stop flag (the final labels pass)
 };
 
 struct GenericArgs {
@@ -127,6 +129,8 @@ struct GenericArgs {
   float A_max;
   const float* B_max_ptr;          // max_k ||c~_k||^2, written by the update kernel
   float tau;
+  int store_labels;                // as in FastArgs
+  int ignore_done;
 };
 
 // ---- tensor-core path (d = 64) and sorted mean calculation ----

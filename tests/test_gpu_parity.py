@@ -260,3 +260,74 @@ def test_full_scale_offset_n2p27_sampled(km, oracle):
         assert np.linalg.norm(mu[c] - ref) <= 1e-6 * max(np.linalg.norm(ref), 1.0)
     assert g.stats()["path"] == 1
     g.close()
+
+
+@pytest.mark.parametrize("case", ["fused_2d", "fused_k256", "generic_d5"])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_label_policy_final(km, oracle, case, use_graph):
+    """The "final" label policy: the steps skip the label writes, km_run ends
+    with one assignment pass against the returned centroids.  Centroids,
+    iteration count and E are bit-identical to the every-step run; the labels
+    are the oracle's assignment to the returned centroids."""
+    if case == "fused_2d":
+        w = synth.workload("plain_2d_n1e5_k8")
+        x, mu0, k = w["x"], w["mu0"], w["k"]
+    elif case == "fused_k256":
+        x, _, _ = synth.iso_mixture(120_001, 3, 256, sigma=1.0, box=50.0, seed=31, weights="dirichlet")
+        mu0, _ = synth.init_distinct(x, 256, seed=32)
+        k = 256
+    else:
+        x, _, _ = synth.iso_mixture(30_007, 5, 3, sigma=1.0, box=5.0, seed=33)
+        mu0, _ = synth.init_distinct(x, 3, seed=34)
+        k = 3
+    d, n = x.shape
+    out = {}
+    for pol in ("every_step", "final"):
+        g = km.KMeans(n, d, k, label_policy=pol, use_graph=use_graph)
+        g.set_points(x)
+        g.set_init(mu0)
+        out[pol] = (g.run(60, 1e-6), g.counts(), g.objective(), g.stats()["path"])
+        g.close()
+    (ra, ca, _, pa), (rb, cb, ob, pb) = out["every_step"], out["final"]
+    assert pa == pb and pa in (1, 2)
+    assert ra["iters"] == rb["iters"] and ra["E"] == rb["E"]
+    assert np.array_equal(ra["centroids"], rb["centroids"])
+    assert np.array_equal(ca, cb)
+    z_ref = oracle.assign(x, rb["centroids"])
+    assert np.array_equal(rb["labels"], z_ref), np.flatnonzero(rb["labels"] != z_ref)[:10]
+    xd = x.astype(np.float64)
+    obj = sum(float(((xd[:, z_ref == c] - rb["centroids"][c][:, None]) ** 2).sum()) for c in range(k))
+    assert abs(ob - obj) <= 1e-9 * max(obj, 1.0)
+
+
+def test_label_policy_final_step_api(km, oracle):
+    """Under the "final" policy km_step leaves the labels alone; write_labels
+    then gives the assignment to the current centroids."""
+    x, _, _ = synth.aniso_mixture(50_000, 3, 8, seed=41)
+    mu0, _ = synth.init_distinct(x, 8, seed=42)
+    g = km.KMeans(x.shape[1], 3, 8, label_policy="final")
+    g.set_points(x)
+    g.set_init(mu0)
+    g.step()
+    assert not g.labels().any()          # never written: the buffer's initial zeros
+    _, mu1, cnt1, _ = oracle.step(x, mu0)
+    assert np.array_equal(g.counts(), cnt1)
+    g.write_labels()
+    assert np.array_equal(g.labels(), oracle.assign(x, g.centroids()))
+    g.close()
+
+
+def test_dist_path_option(km, oracle):
+    """dist_path: "simt" keeps d = 64 off the tensor cores (generic FP32
+    path, same bit-exact labels); "tensor" on a shape the tcgen05 path does
+    not take is an argument error; "tensor" on d = 64 selects it."""
+    x, _, _ = synth.iso_mixture(20_000, 64, 40, sigma=1.0, box=8.0, seed=51)
+    mu0, _ = synth.init_distinct(x, 100, seed=52)
+    st = lockstep(km, oracle, x, mu0, steps=1, dist_path="simt")
+    assert st["path"] == 2
+    g = km.KMeans(x.shape[1], 64, 100, dist_path="tensor")
+    assert g.stats()["path"] == 3
+    g.close()
+    with pytest.raises(km.KMError) as ei:
+        km.KMeans(1000, 3, 8, dist_path="tensor")
+    assert ei.value.status == -1
