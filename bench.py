@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--label-policy", default="every_step", choices=["every_step", "final"],
                     help="write the N labels every step, or once after the last step")
+    ap.add_argument("--tc-operands", default="bf16", choices=["bf16", "f16"],
+                    help="operand type of the tensor-core distances (d = 64)")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batch workloads")
     ap.add_argument("--learned-count", type=int, default=6, help="held-out mixtures of the learned-init workload")
     ap.add_argument("--plain-every", type=int, default=1,
@@ -267,7 +269,7 @@ def run_ours(args, ws, rank, local):
     d, n = x.shape
     xt = torch.from_numpy(x).to(dev)
     stream = torch.cuda.current_stream(dev)
-    g = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy)
+    g = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy, tc_operands=args.tc_operands)
     g.set_points(xt, borrow=True)
     g.set_init(mu0)
     K, W = args.steps, args.warmup
@@ -314,7 +316,7 @@ def run_ours(args, ws, rank, local):
     xp = torch.from_numpy(x).pin_memory()
     lab_out = torch.empty(n, dtype=torch.int32).pin_memory()
     e2e_times = []
-    g2 = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy)
+    g2 = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy, tc_operands=args.tc_operands)
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -348,10 +350,11 @@ def run_ours(args, ws, rank, local):
         peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0)))
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "gemm_assign_kernel (tcgen05 BF16) + gemm_rescue_kernel",
+                "kernel": f"gemm_assign_kernel (tcgen05 {args.tc_operands.upper()}) + gemm_tie_kernel + "
+                          f"gemm_rescue_kernel",
                 "kernel_ms": assign_ms,
-                "peak_source": f"bf16 dense, sustained, {src} peaks; algorithmic 2*N*K*d flops per launch "
-                               f"(the GEMM form's contraction)",
+                "peak_source": f"bf16 dense, sustained, {src} peaks (f16 has the same nominal dense rate); "
+                               f"algorithmic 2*N*K*d flops per launch (the GEMM form's contraction)",
                 "hbm_frac_of_measured": (n * d * 2 / (assign_ms / 1e3) / 1e9) / float(pk.get("hbm_gbs", 6800.0))}
     else:
         fp32_peak_tflops = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
@@ -364,7 +367,7 @@ def run_ours(args, ws, rank, local):
                 "hbm_frac_of_measured": (n * d * 4 / (assign_ms / 1e3) / 1e9) / float(pk.get("hbm_gbs", 6800.0))}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "vs_baseline": None, "dtype": args.tc_operands if stats["path"] == 3 else "f32", "data": "synthetic",
            "config": {"workload": args.workload, "n": n, "d": d, "k": k,
                       "init": "k-means++ on a 2^20-point subsample" if "n1e8" in args.workload or "n2p27" in args.workload
                               else "seeded distinct points",
@@ -377,7 +380,8 @@ def run_ours(args, ws, rank, local):
            "assign_ms": assign_ms, "update_ms": ms_step - assign_ms,
            "flagged_per_step": stats["flagged"], "fp64_decided_per_step": stats["fp64_decided"],
            "overflowed_per_step": stats["overflowed"],
-           "path": {1: "fused FFMA2", 2: "generic", 3: "tcgen05 BF16 GEMM-form"}.get(stats["path"])}
+           "path": {1: "fused FFMA2", 2: "generic",
+                    3: f"tcgen05 {args.tc_operands.upper()} GEMM-form"}.get(stats["path"])}
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     g.close()
@@ -529,6 +533,81 @@ def run_learned(args, ws, rank, local):
     return 0
 
 
+# The paper's OpenACC times to converge (seconds; its own data, random start
+# and unnamed GPU: context only), tables 4 and 5.
+PAPER_OPENACC_S = {("2d", 100_000, 8): 0.7213, ("2d", 200_000, 8): 0.283524, ("2d", 500_000, 8): 0.518219,
+                   ("3d", 100_000, 4): 0.087148, ("3d", 200_000, 4): 0.486771, ("3d", 400_000, 4): 0.548548,
+                   ("3d", 800_000, 4): 0.743832, ("3d", 1_000_000, 4): 0.802407}
+
+
+def run_sweep(args, ws, rank, local):
+    """The paper's problem sizes, each to convergence (tol 1e-6, at most 300
+    steps) from seeded distinct points: time to converge with the points
+    resident on the device (km_run, its graph built by one untimed run),
+    end to end from host arrays (points in, labels and centroids out), and
+    the FP64 oracle's time to converge on the host cores from the same start.
+    Iteration counts and labels are compared with the oracle's."""
+    import numpy as np
+    import synth
+    import oracle
+    cases = [(kind, n, k, synth.sweep_case(kind, n, k)) for kind, n, k in synth.paper_sweep()]
+    import torch
+    import paper_2405_12052_gb300 as km
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    km.build()
+    orc = oracle.default()
+    rows, evals, gpu_s = [], 0, 0.0
+    for kind, n, k, w in cases:
+        x, mu0 = w["x"], w["mu0"]
+        d = x.shape[0]
+        xt = torch.from_numpy(x).to(dev)
+        g = km.KMeans(n, d, k)
+        g.set_points(xt, borrow=True)
+        times = []
+        for _ in range(1 + max(1, args.steps // 100)):
+            g.set_init(mu0)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            r = g.run(w["max_iter"], w["tol"])
+            times.append(time.perf_counter() - t0)
+        t_dev = statistics.median(times[1:])
+        g.close()
+        t0 = time.perf_counter()
+        g2 = km.KMeans(n, d, k)
+        g2.set_points(x)
+        g2.set_init(mu0)
+        r2 = g2.run(w["max_iter"], w["tol"])
+        t_e2e = time.perf_counter() - t0
+        g2.close()
+        t0 = time.perf_counter()
+        ref = orc.run(x, mu0, w["max_iter"], w["tol"])
+        t_orc = time.perf_counter() - t0
+        same = (r["iters"] == ref["iters"] and np.array_equal(r["labels"], ref["labels"])
+                and np.array_equal(r2["labels"], ref["labels"]))
+        evals += n * k * r["iters"]
+        gpu_s += t_dev
+        rows.append({"d": d, "n": n, "k": k, "iters": r["iters"], "oracle_iters": ref["iters"],
+                     "same_labels_and_iters_as_oracle": bool(same),
+                     "gpu_time_to_converge_ms": 1e3 * t_dev, "gpu_us_per_iter": 1e6 * t_dev / max(1, r["iters"]),
+                     "e2e_time_to_converge_ms": 1e3 * t_e2e, "oracle_time_to_converge_ms": 1e3 * t_orc,
+                     "paper_openacc_s": PAPER_OPENACC_S.get((kind, n, k))})
+    out = {"metric": METRIC, "value": evals / gpu_s, "unit": UNIT, "n_gpus": 1, "steps": sum(r["iters"] for r in rows),
+           "warmup": 1, "ms_per_step": 1e3 * gpu_s / max(1, sum(r["iters"] for r in rows)),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "paper_sweep", "cases": len(rows), "tol": 1e-6, "max_iter": 300,
+                      "init": "seeded distinct points", "l2": "L2-resident (at most 12 MB of points)",
+                      "parallelism": "single"},
+           "clocks": None, "e2e": None, "gpu_launches": None,
+           "note": "time to converge per size; the paper's OpenACC seconds are its own data, start and GPU "
+                   "(context, not comparable)",
+           "oracle_cores": orc.threads(), "sweep": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -538,6 +617,8 @@ def main():
         return run_batch(args, ws, rank, local)
     if args.workload.startswith("learned"):
         return run_learned(args, ws, rank, local)
+    if args.workload == "paper_sweep":
+        return run_sweep(args, ws, rank, local)
     return run_ours(args, ws, rank, local)
 
 

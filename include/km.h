@@ -66,6 +66,7 @@ enum { KM_HOST = 0, KM_DEVICE_COPY = 1, KM_DEVICE_BORROW = 2 }; /* where a buffe
 enum { KM_E_NORM = 0, KM_E_SQUARED = 1 };                      /* which error km_run tests */
 enum { KM_LABELS_EVERY_STEP = 0, KM_LABELS_FINAL = 1 };         /* label write policy */
 enum { KM_DIST_AUTO = 0, KM_DIST_SIMT = 1, KM_DIST_TENSOR = 2 }; /* distance path */
+enum { KM_TC_BF16 = 0, KM_TC_F16 = 1 };                         /* tensor-core operand type */
 
 typedef struct km_options {
   int32_t e_mode;  /* KM_E_NORM (default): stop when sqrt(E^2) < tol;
@@ -83,6 +84,11 @@ typedef struct km_options {
   int32_t dist_path;    /* KM_DIST_AUTO (default): tensor cores for d = 64 and K <= 1024,
                            else FP32 SIMT; KM_DIST_SIMT: FP32 SIMT kernels always;
                            KM_DIST_TENSOR: the tcgen05 path or KM_EINVAL */
+  int32_t tc_operands;  /* operands of the tcgen05 distances: KM_TC_BF16 (default; 8
+                           significand bits) or KM_TC_F16 (11 bits, same tensor rate;
+                           points and centres scaled by powers of two into FP16's
+                           range), so a candidate window 8x narrower; the labels are
+                           exact either way */
 } km_options;
 
 /* Fill *opt with the defaults above. */

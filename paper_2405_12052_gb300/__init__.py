@@ -40,11 +40,13 @@ class KMError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("e_mode", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("tie_rel", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("label_policy", ctypes.c_int32), ("dist_path", ctypes.c_int32)]
+                ("label_policy", ctypes.c_int32), ("dist_path", ctypes.c_int32),
+                ("tc_operands", ctypes.c_int32)]
 
 
 LABEL_POLICIES = {"every_step": 0, "final": 1}
 DIST_PATHS = {"auto": 0, "simt": 1, "tensor": 2}
+TC_OPERANDS = {"bf16": 0, "f16": 1}
 
 
 class _Stats(ctypes.Structure):
@@ -204,7 +206,7 @@ class KMeans:
 
     def __init__(self, n: int, d: int, k: int, *, e_mode: str = "norm", tie_rel: float = 1e-5,
                  use_graph: bool = True, stream=None, label_policy: str = "every_step",
-                 dist_path: str = "auto"):
+                 dist_path: str = "auto", tc_operands: str = "bf16"):
         self._L = lib()
         self.n, self.d, self.k = int(n), int(d), int(k)
         opt = _Options()
@@ -212,6 +214,7 @@ class KMeans:
         opt.e_mode = E_MODES[e_mode]
         opt.label_policy = LABEL_POLICIES[label_policy]
         opt.dist_path = DIST_PATHS[dist_path]
+        opt.tc_operands = TC_OPERANDS[tc_operands]
         opt.use_graph = 1 if use_graph else 0
         opt.tie_rel = float(tie_rel)
         if stream is None:

@@ -72,6 +72,7 @@ struct km_ctx {
   double* bnorm = nullptr;
   int ms_max_chunks = 0;
   float A_max = 0.f;
+  int tc_ex = 0;           // FP16 tensor-core operands: points scaled by 2^tc_ex
   int G0 = 0;
   // loop
   cudaGraphExec_t graph = nullptr;
@@ -130,6 +131,7 @@ GemmPrepArgs gemm_prep_args(km_ctx* c) {
   g.mu = c->mu; g.shift = c->shift; g.k = c->k; g.kpad = c->kpad;
   g.cb = c->cbf; g.nprime = c->nprime; g.ctil = c->ctil; g.gc = c->gc;
   g.A_max = c->A_max; g.tie_rel = c->opt.tie_rel; g.ls = c->ls; g.bnorm = c->bnorm;
+  g.f16 = c->opt.tc_operands == KM_TC_F16 ? 1 : 0; g.ex = c->tc_ex;
   return g;
 }
 
@@ -163,6 +165,7 @@ cudaError_t launch_assign(km_ctx* c, bool labels_pass = false) {
     g.rescue_list = c->rescue_list; g.tie_list = c->tie_list;
     g.rescue_count = c->rescue_count; g.tie_count = c->rescue_count + 1;
     g.n = c->n; g.k = c->k; g.kpad = c->kpad; g.ntiles = (int)((c->n + 127) / 128);
+    g.f16 = c->opt.tc_operands == KM_TC_F16 ? 1 : 0;
     return launch_gemm_assign(c->G, c->st, g);
   }
   if (c->fast) {
@@ -243,6 +246,7 @@ void km_default_options(km_options* opt) {
   opt->stream = nullptr;
   opt->label_policy = KM_LABELS_EVERY_STEP;
   opt->dist_path = KM_DIST_AUTO;
+  opt->tc_operands = KM_TC_BF16;
 }
 
 const char* km_version(void) { return "libkm 0.1 (sm_103a)"; }
@@ -263,6 +267,8 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
     return fail(c, KM_EINVAL, "label_policy out of range");
   if (c->opt.dist_path < KM_DIST_AUTO || c->opt.dist_path > KM_DIST_TENSOR)
     return fail(c, KM_EINVAL, "dist_path out of range");
+  if (c->opt.tc_operands != KM_TC_BF16 && c->opt.tc_operands != KM_TC_F16)
+    return fail(c, KM_EINVAL, "tc_operands out of range");
   if (c->opt.e_mode != KM_E_NORM && c->opt.e_mode != KM_E_SQUARED) return fail(c, KM_EINVAL, "bad e_mode");
   KM_CUDA(c, cudaGetDevice(&c->dev));
   cudaDeviceProp p{};
@@ -445,7 +451,16 @@ km_status km_set_points(km_ctx* c, const float* x, int64_t ld, int32_t layout, i
   KM_CUDA(c, cudaMemcpyAsync(c->dc, &hdc, sizeof(hdc), cudaMemcpyHostToDevice, c->st));
   KM_CUDA(c, cudaStreamSynchronize(c->st));
   if (c->path == 3) {
-    KM_CUDA(c, launch_gemm_prep_points(c->x, c->ld, n, c->shift, c->xb, c->xa_pt, c->xaos, c->st));
+    // FP16 operands: |fl(x_j - s_j)| <= sqrt(A_max) scaled to at most 2^14
+    c->tc_ex = 0;
+    if (c->opt.tc_operands == KM_TC_F16 && ha > 0.f) {
+      const double xm = std::sqrt((double)ha) * 1.001;
+      int e = (int)std::floor(std::log2(16384.0 / xm));
+      while (e > -200 && std::ldexp(xm, e) > 16384.0) --e;
+      c->tc_ex = std::max(-100, std::min(100, e));
+    }
+    KM_CUDA(c, launch_gemm_prep_points(c->x, c->ld, n, c->shift, c->xb, c->xa_pt, c->xaos,
+                                       c->opt.tc_operands == KM_TC_F16 ? 1 : 0, c->tc_ex, c->st));
     KM_CUDA(c, cudaStreamSynchronize(c->st));
   }
   c->have_points = true;

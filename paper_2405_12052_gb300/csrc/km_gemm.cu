@@ -1,5 +1,5 @@
 // Reassignment for d = 64 in the GEMM form ||c||^2 - 2 x.c on the 5th-gen
-// tensor cores (tcgen05, BF16 operands, FP32 accumulation in TMEM), the
+// tensor cores (tcgen05, BF16 or FP16 operands, FP32 accumulation in TMEM), the
 // expectation step of Lloyd's algorithm (paper, section "The Lloyd's
 // algorithm", step 2) where d is large enough for a dense contraction.
 //
@@ -17,7 +17,7 @@
 //    stored whole to shared memory (up to kSlots halves per point, 16 bits
 //    per value relative to the half's minimum).  The threshold is the
 //    best r seen so far plus the candidate window Delta(x), which bounds every
-//    BF16 and FP32 rounding of the screen plus the oracle's FP64 error and
+//    operand and FP32 rounding of the screen plus the oracle's FP64 error and
 //    1e-5 D, so the kept set always holds the exact argmin and all near ties.
 //    For the first group the epilogue takes two passes (minima, a barrier,
 //    then the stores), so the threshold already covers 256 centroids.
@@ -28,7 +28,11 @@
 //    did not fit go to a list that a second kernel resolves exactly over all
 //    K (a fraction of a percent of points on split clusters).
 // Labels only; the sums are formed by the sorted mean calculation.
+// FP16 operands: the points are scaled by 2^ex (fixed with the points) and
+// the centres by 2^ec (per step) so every coordinate is at most 2^14 in
+// magnitude; the product is unscaled exactly in the epilogue's factor.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -46,7 +50,7 @@ constexpr int kGThreads = kEpiThreads + 32;  // + the producer warp
 constexpr int kSlots = 12;        // stored halves per point
 constexpr int kHalf = 16;         // values per stored half
 constexpr int kPtStride = kSlots * kHalf * 2 + 16;  // bytes per point (padding spreads banks)
-constexpr int kTileBytes = kGM * kGemmD * 2;   // 16 KB of BF16 per point tile
+constexpr int kTileBytes = kGM * kGemmD * 2;   // 16 KB of 16-bit operands per point tile
 constexpr int kTieMax = 20;       // candidates per near-tie list entry (48 bytes)
 constexpr long kWaitLimit = 1L << 22;
 // shared-memory layout (bytes from the 1024-aligned base)
@@ -68,13 +72,14 @@ __device__ __forceinline__ uint64_t sm_desc(uint32_t saddr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// D(128 x 256, f32) += A(128 x 16, bf16, K-major) x B(256 x 16, bf16, K-major)^T
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kGN >> 3) << 17) |
-                            ((uint32_t)(kGM >> 4) << 24);
+// D(128 x 256, f32) += A(128 x 16, K-major) x B(256 x 16, K-major)^T with A
+// and B both BF16 (A and B type fields 1) or both FP16 (fields 0)
+constexpr uint32_t kIdescF16 = (1u << 4) | ((uint32_t)(kGN >> 3) << 17) | ((uint32_t)(kGM >> 4) << 24);
+constexpr uint32_t kIdescBF16 = kIdescF16 | (1u << 7) | (1u << 10);
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+__device__ __forceinline__ void mma_16bit(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-               ::"r"(tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+               ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -262,6 +267,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
     if (lane == 0) {
       const uint32_t sC_addr = (uint32_t)__cvta_generic_to_shared(sC);
       const uint32_t sA_addr = (uint32_t)__cvta_generic_to_shared(sA);
+      const uint32_t idesc = a.f16 ? kIdescF16 : kIdescBF16;
       const unsigned char* xb = reinterpret_cast<const unsigned char*>(a.xb);
       auto load_tile = [&](int l) {
         const int s = l & 1;
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
             const uint32_t abase = sA_addr + s * kTileBytes, bbase = sC_addr + (uint32_t)(g * kGN * 128);
 #pragma unroll
             for (int kk = 0; kk < kGemmD / 16; ++kk)
-              mma_bf16(d, sm_desc(abase + kk * 32), sm_desc(bbase + kk * 32), kk > 0 ? 1u : 0u);
+              mma_16bit(d, sm_desc(abase + kk * 32), sm_desc(bbase + kk * 32), idesc, kk > 0 ? 1u : 0u);
             mma_commit(bar_addr(4 + b));
             if (g == 0 && pending >= 0) {
               // tile pending's MMAs were queued before this group: its stage
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
       nA = i1 < a.n ? a.xa[i1] : 0.f;
     };
     // Start threshold of tile l from each point's previous label z (any
-    // label in range bounds the minimum): r_z from the resident BF16
+    // label in range bounds the minimum): r_z from the resident 16-bit
     // operands, 4 threads per point with 16 coordinates each, plus the window
     // and a bound on its difference from the tensor-core value of r_z.
     // Computed before the barrier that ends the previous tile, which
@@ -364,11 +370,17 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
           const int c = 2 * sub + h;  // 16-byte chunk: coordinates 8c .. 8c+7
           const uint4 xv = *reinterpret_cast<const uint4*>(xr + pp * 128 + ((c ^ (pp & 7)) << 4));
           const uint4 cv = *reinterpret_cast<const uint4*>(sC + (size_t)z * 128 + ((c ^ (z & 7)) << 4));
-          const __nv_bfloat162* xh = reinterpret_cast<const __nv_bfloat162*>(&xv);
-          const __nv_bfloat162* ch = reinterpret_cast<const __nv_bfloat162*>(&cv);
+          const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w}, cw[4] = {cv.x, cv.y, cv.z, cv.w};
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float2 xf = __bfloat1622float2(xh[q]), cf = __bfloat1622float2(ch[q]);
+            float2 xf, cf;
+            if (a.f16) {
+              xf = __half22float2(*reinterpret_cast<const __half2*>(&xw[q]));
+              cf = __half22float2(*reinterpret_cast<const __half2*>(&cw[q]));
+            } else {
+              xf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xw[q]));
+              cf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&cw[q]));
+            }
             S = __fmaf_rn(xf.x, cf.x, S);
             S = __fmaf_rn(xf.y, cf.y, S);
           }
@@ -738,17 +750,19 @@ __global__ void __launch_bounds__(256) gemm_rescue_kernel(GemmArgs a) {
   if (lane == 0 && n64) atomicAdd(&a.ls->fp64_decided, (unsigned long long)n64);
 }
 
-// Points -> BF16 shifted rows in the swizzled tile layout, ||x~||^2 (rounded
-// up) and an N x d FP32 copy.
+// Points -> 16-bit shifted rows in the swizzled tile layout (BF16, or FP16
+// of 2^ex fl(x - s): an exact power-of-two scaling), ||x~||^2 (rounded up)
+// and an N x d FP32 copy.
 __global__ void gemm_prep_points_kernel(const float* __restrict__ x, int64_t ld, int64_t n, const float* shift,
-                                        __nv_bfloat16* xb, float* xa, float* xaos) {
+                                        unsigned short* xb, float* xa, float* xaos, int f16, float xscale) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float A = 0.f;
     for (int j = 0; j < kGemmD; ++j) {
       const float v = x[(int64_t)j * ld + i];
       const float t = __fsub_rn(v, shift[j]);
       xaos[i * kGemmD + j] = v;
-      xb[swz_index(i, j)] = __float2bfloat16_rn(t);
+      xb[swz_index(i, j)] = f16 ? __half_as_ushort(__float2half_rn(t * xscale))
+                                : __bfloat16_as_ushort(__float2bfloat16_rn(t));
       A = __fmaf_ru(t, t, A);
     }
     xa[i] = A;
@@ -756,8 +770,9 @@ __global__ void gemm_prep_points_kernel(const float* __restrict__ x, int64_t ld,
 }
 
 // Tables of the next step from mu, one thread per centroid: BF16 rows in the
-// swizzled layout, FP32 c~ rows and B_k = ||mu_k - s||^2 (FP64, coordinates
-// in order).
+// swizzled layout (FP16 rows are written by the consts kernel, which knows
+// their scale), FP32 c~ rows and B_k = ||mu_k - s||^2 (FP64, coordinates in
+// order).
 __global__ void __launch_bounds__(64) gemm_tables_kernel(GemmPrepArgs a) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= a.kpad) return;
@@ -771,15 +786,16 @@ __global__ void __launch_bounds__(64) gemm_tables_kernel(GemmPrepArgs a) {
       a.ctil[(size_t)c * kGemmD + j] = cv;
       B = __dadd_rn(B, __dmul_rn(t, t));
     }
-    cb[swz_index(c, j)] = __float2bfloat16_rn(cv);
+    if (!a.f16) cb[swz_index(c, j)] = __float2bfloat16_rn(cv);
   }
   a.bnorm[c] = c < a.k ? B : 0.0;
 }
 
-// The scale and window constants from max_k B_k (one block), then n'_k.
+// The scale and window constants from max_k B_k (one block), then n'_k and,
+// for FP16 operands, the centre rows scaled by 2^ec.
 __global__ void __launch_bounds__(256) gemm_consts_kernel(GemmPrepArgs a) {
   __shared__ double s_max[256];
-  __shared__ int s_sigma;
+  __shared__ int s_sigma, s_ec;
   const int k = a.k, kpad = a.kpad;
   double m = 0.0;
   for (int c = threadIdx.x; c < k; c += blockDim.x) m = fmax(m, a.bnorm[c]);
@@ -798,20 +814,43 @@ __global__ void __launch_bounds__(256) gemm_consts_kernel(GemmPrepArgs a) {
     sigma = max(-120, min(120, sigma));
     s_sigma = sigma;
     const double u = 0x1p-24, tw = ldexp(1.0, sigma);
-    const double epsS = 0x1p-7 * 1.0003 + 0x1p-16;  // BF16 products + FP32 accumulation
     const double sB = sqrt(bmax);
+    // FP16: every |c~_kj| <= sqrt(B_max) is scaled to at most 2^14 (FP16
+    // holds up to 65504), unless that would push the epilogue's factor
+    // 2^(sigma + 1 - ex - ec) below FP32's normal range
+    int ec = 0;
+    double uop = 0x1p-8, ax = 0.0, ac = 0.0;
+    if (a.f16) {
+      const double cm = sB * 1.001 + 1e-300;
+      ec = (int)floor(log2(0x1p14 / cm));
+      while (ec > -200 && ldexp(cm, ec) > 0x1p14) --ec;
+      ec = max(-100, min(ec, min(100, sigma + 126 - a.ex)));
+      uop = 0x1p-11;
+      ax = ldexp(0x1p-25, -a.ex);  // absolute rounding of a scaled value below 2^-14 (subnormal)
+      ac = ldexp(0x1p-25, -ec);
+    }
+    s_ec = ec;
+    // one operand: |fl16(fl32(t)) - t| <= (uop + 2^-24) |t| + a; a product of
+    // two: (2 v + v^2) |x||c| + (1 + v)(a_c |x| + a_x |c|) + a_x a_c with
+    // v = uop + 2^-24; summed over 64 coordinates (||.||_1 <= 8 ||.||) plus
+    // the FP32 accumulation of 64 products in any order (<= 2^-16 sum |p|)
+    const double v = uop + 0x1p-24;
+    const double epsS = 2.0 * v + v * v + 0x1p-16;
     const double gam = 2.0 * 4.1 * (kGemmD + 1) * 0x1p-53;
     GemmConst g;
-    g.scale = -(float)ldexp(1.0, sigma + 1);
+    g.scale = -(float)ldexp(1.0, sigma + 1 - (a.f16 ? a.ex + ec : 0));
     g.M = 1.5f;
     // Delta(x) = c0 + ||x~|| c1 + ||x~||^2 cA (units of r): two screen errors
-    // 2 epsS ||x~|| ||c~|| + u h each, the oracle's FP64 error, tie_rel * D2
-    // with D2 <= (||x~|| + ||c~||)^2, four ulps of the binade
-    g.c0 = (float)((tw * (2.0 * u * bmax + gam * bmax + a.tie_rel * bmax) + 8.0 * 0x1p-23) * (1.0 + 1e-3));
-    g.c1 = (float)(tw * (4.0 * epsS * sB + 2.0 * a.tie_rel * sB) * (1.0 + 1e-3));
+    // 2 (epsS ||x~|| ||c~|| + 8 (1 + v)(a_c ||x~|| + a_x ||c~||) + 64 a_x a_c) + u h
+    // each, the oracle's FP64 error, tie_rel * D2 with D2 <= (||x~|| + ||c~||)^2,
+    // four ulps of the binade
+    g.c0 = (float)((tw * (2.0 * u * bmax + gam * bmax + a.tie_rel * bmax + 4.0 * (8.0 * (1.0 + v) * ax * sB +
+                                                                                64.0 * ax * ac)) +
+                    8.0 * 0x1p-23) * (1.0 + 1e-3));
+    g.c1 = (float)(tw * (4.0 * epsS * sB + 2.0 * a.tie_rel * sB + 4.0 * 8.0 * (1.0 + v) * ac) * (1.0 + 1e-3));
     g.cA = (float)(tw * (gam + a.tie_rel) * (1.0 + 1e-3));
     // start estimate: |r_est - r_tc| <= 2^(sigma+1) (2^-16 + 2^-18) ||x_b|| ||c_b|| (two FP32
-    // sums of 64 BF16 products in different orders), taken as 2^-14 per unit ||x~||
+    // sums of 64 products of 16-bit operands in different orders), taken as 2^-14 per unit ||x~||
     g.cest = (float)(2.0 * tw * 0x1p-14 * sB);
     g.B_max = (float)(bmax * (1.0 + 1e-6));
     g.tau = (float)(a.tie_rel * (1.0 + 1e-4));
@@ -823,6 +862,15 @@ __global__ void __launch_bounds__(256) gemm_consts_kernel(GemmPrepArgs a) {
   // padding columns: r = 4, far above any real r < 2 plus the window
   for (int c = threadIdx.x; c < kpad; c += blockDim.x)
     a.nprime[c] = c < k ? __double2float_rn(1.5 + tw * a.bnorm[c]) : 4.0f;
+  if (a.f16) {
+    const float cs = ldexpf(1.f, s_ec);
+    unsigned short* cb = reinterpret_cast<unsigned short*>(a.cb);
+    for (int q = threadIdx.x; q < kpad * kGemmD; q += blockDim.x) {
+      const int c = q / kGemmD, j = q - c * kGemmD;
+      const float cv = c < k ? a.ctil[(size_t)c * kGemmD + j] : 0.f;
+      cb[swz_index(c, j)] = __half_as_ushort(__float2half_rn(cv * cs));
+    }
+  }
 }
 
 }  // namespace
@@ -851,13 +899,13 @@ cudaError_t launch_gemm_assign(int grid, cudaStream_t st, const GemmArgs& a) {
 }
 
 cudaError_t launch_gemm_prep_points(const float* x, int64_t ld, int64_t n, const float* shift, void* xb, float* xa,
-                                    float* xaos, cudaStream_t st) {
+                                    float* xaos, int f16, int ex, cudaStream_t st) {
   // rows past N (to the next tile boundary) stay zero
   cudaError_t e = cudaMemsetAsync(xb, 0, (size_t)gemm_xb_rows(n) * kGemmD * 2, st);
   if (e != cudaSuccess) return e;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
-  gemm_prep_points_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, ld, n, shift, reinterpret_cast<__nv_bfloat16*>(xb),
-                                                            xa, xaos);
+  gemm_prep_points_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, ld, n, shift, reinterpret_cast<unsigned short*>(xb),
+                                                            xa, xaos, f16, std::ldexp(1.f, ex));
   return cudaGetLastError();
 }
 

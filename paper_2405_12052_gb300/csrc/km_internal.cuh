@@ -149,7 +149,7 @@ struct GemmConst {
 };
 
 struct GemmArgs {
-  const void* xb;        // [ceil(N/128)*128][64] BF16 rows of fl(x - s), 128-byte swizzled (__nv_bfloat16)
+  const void* xb;        // [ceil(N/128)*128][64] BF16 (or scaled FP16) rows of fl(x - s), 128-byte swizzled
   const float* xa;       // [N] ||fl(x - s)||^2, rounded up
   const float* xaos;     // [N][64] FP32 points
   const void* cb;        // [kpad][64] BF16 rows of fl(mu - s), 128-byte swizzled
@@ -166,6 +166,7 @@ struct GemmArgs {
   unsigned* tie_count;     // = rescue_count + 1
   int64_t n;
   int k, kpad, ntiles;
+  int f16;               // operands are FP16 (scaled by powers of two), else BF16
 };
 
 struct GemmPrepArgs {
@@ -173,6 +174,8 @@ struct GemmPrepArgs {
   void* cb; float* nprime; float* ctil; GemmConst* gc;
   double* bnorm;                   // [kpad] ||mu_k - s||^2
   float A_max; double tie_rel;
+  int f16;                         // FP16 operands: cb written by the consts kernel, scaled by 2^ec
+  int ex;                          // FP16: the points were scaled by 2^ex
   const LoopState* ls;
 };
 
@@ -194,7 +197,7 @@ struct MsortArgs {
 
 cudaError_t launch_gemm_assign(int grid, cudaStream_t st, const GemmArgs& a);
 cudaError_t launch_gemm_prep_points(const float* x, int64_t ld, int64_t n, const float* shift, void* xb, float* xa,
-                                    float* xaos, cudaStream_t st);
+                                    float* xaos, int f16, int ex, cudaStream_t st);
 cudaError_t launch_gemm_prepare(cudaStream_t st, const GemmPrepArgs& a);
 size_t gemm_smem_bytes(int kpad);
 int64_t gemm_xb_rows(int64_t n);

@@ -226,12 +226,17 @@ def workload(name: str, **kw) -> dict:
 
 def paper_sweep():
     """The paper's size sweep (tables 2-5): 2D N in {1e5, 2e5, 5e5} at K=8 and
-    3D N in {1e5, 2e5, 4e5, 8e5, 1e6} at K=4."""
+    3D N in {1e5, 2e5, 4e5, 8e5, 1e6} at K=4, plus table 1's cluster counts
+    (2D N = 5e5 and 3D N = 1e6 at K = 4, 8, 11)."""
     out = []
     for n in (100_000, 200_000, 500_000):
         out.append(("2d", n, 8))
     for n in (100_000, 200_000, 400_000, 800_000, 1_000_000):
         out.append(("3d", n, 4))
+    for k in (4, 11):
+        out.append(("2d", 500_000, k))
+    for k in (8, 11):
+        out.append(("3d", 1_000_000, k))
     return out
 
 
