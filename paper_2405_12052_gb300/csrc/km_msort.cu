@@ -85,6 +85,94 @@ __global__ void ms_scatter_kernel(const int32_t* __restrict__ labels, int64_t n,
   }
 }
 
+// The same scatter with one global reservation per (block, label): a block
+// takes kScatterPts consecutive points, counts their labels in shared
+// memory, reserves each label's run with one atomic on the cluster's cursor
+// and places its points by shared-memory ranks (K <= kScatterMaxK).
+constexpr int kScatterPts = 4096;
+constexpr int kScatterMaxK = 4096;
+__global__ void __launch_bounds__(256) ms_scatter_block_kernel(const int32_t* __restrict__ labels, int64_t n, int k,
+                                                               const int64_t* __restrict__ offsets,
+                                                               unsigned long long* cursor, int32_t* perm) {
+  extern __shared__ unsigned long long s_base[];  // [k] run starts, then [k] u32 counts / ranks
+  unsigned int* s_cnt = reinterpret_cast<unsigned int*>(s_base + k);
+  const int64_t i0 = (int64_t)blockIdx.x * kScatterPts;
+  const int64_t i1 = min(n, i0 + kScatterPts);
+  for (int c = threadIdx.x; c < k; c += blockDim.x) s_cnt[c] = 0u;
+  __syncthreads();
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) atomicAdd(&s_cnt[labels[i]], 1u);
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    const unsigned m = s_cnt[c];
+    if (m) s_base[c] = (unsigned long long)offsets[c] + atomicAdd(&cursor[c], (unsigned long long)m);
+    s_cnt[c] = 0u;
+  }
+  __syncthreads();
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const int z = labels[i];
+    const unsigned r = atomicAdd(&s_cnt[z], 1u);
+    perm[s_base[z] + r] = (int32_t)i;
+  }
+}
+
+// Chunk sums with 16-byte loads (d a multiple of 4): threads (r, q) =
+// (threadIdx.x / (d/4), threadIdx.x % (d/4)) sum coordinates 4q..4q+3 of
+// points r, r + R, ... of the chunk, four rows in flight, in int64 fixed
+// point as below.
+__global__ void __launch_bounds__(256) ms_chunk_sum4_kernel(const float4* __restrict__ xa4, int d,
+                                                            const int32_t* __restrict__ perm,
+                                                            const int4* __restrict__ chunks, const int* nchunks,
+                                                            const DataConst* dcp, long long* chunk_sums) {
+  extern __shared__ long long s_part4[];  // [R][d]
+  const int ch = blockIdx.x;
+  if (ch >= *nchunks) return;
+  const int4 cd = chunks[ch];
+  const int d4 = d >> 2;
+  const int R = blockDim.x / d4;
+  const int r = threadIdx.x / d4, q = threadIdx.x - r * d4;
+  const DataConst dc = *dcp;
+  auto fixed = [&](float v) {  // v in grid units of 2^G0, exactly (two FP32 limbs)
+    const float t = __fadd_rn(v, dc.C_hi);
+    const float h = __fsub_rn(t, dc.C_hi);
+    const float rr = __fsub_rn(v, h);
+    const float t2 = __fadd_rn(rr, dc.C_lo);
+    const long long hi = (long long)(int)(__float_as_uint(t) - dc.bits_C_hi);
+    const long long lo = (long long)(int)(__float_as_uint(t2) - dc.bits_C_lo);
+    return (hi << 22) + lo;
+  };
+  long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  auto add = [&](const float4 v) {
+    a0 += fixed(v.x);
+    a1 += fixed(v.y);
+    a2 += fixed(v.z);
+    a3 += fixed(v.w);
+  };
+  if (r < R) {
+    int p = r;
+    for (; p + 3 * R < cd.z; p += 4 * R) {
+      const int i0 = perm[cd.y + p], i1 = perm[cd.y + p + R], i2 = perm[cd.y + p + 2 * R], i3 = perm[cd.y + p + 3 * R];
+      const float4 v0 = xa4[(int64_t)i0 * d4 + q], v1 = xa4[(int64_t)i1 * d4 + q];
+      const float4 v2 = xa4[(int64_t)i2 * d4 + q], v3 = xa4[(int64_t)i3 * d4 + q];
+      add(v0);
+      add(v1);
+      add(v2);
+      add(v3);
+    }
+    for (; p < cd.z; p += R) add(xa4[(int64_t)perm[cd.y + p] * d4 + q]);
+    long long* o = s_part4 + (size_t)r * d + 4 * q;
+    o[0] = a0;
+    o[1] = a1;
+    o[2] = a2;
+    o[3] = a3;
+  }
+  __syncthreads();
+  for (int jj = threadIdx.x; jj < d; jj += blockDim.x) {
+    long long sum = 0;
+    for (int w = 0; w < R; ++w) sum += s_part4[(size_t)w * d + jj];
+    chunk_sums[(size_t)ch * d + jj] = sum;
+  }
+}
+
 // One block per chunk: threads (r, j) = (threadIdx.x / d, threadIdx.x % d)
 // sum coordinate j of points r, r + R, ... of the chunk in int64 fixed point
 // (<= kChunk points of |x| < 2^43 grid units each: no overflow); rows are
@@ -233,11 +321,25 @@ cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st) {
   const size_t hs = a.k <= 8192 ? sizeof(unsigned int) * a.k : 0;
   ms_hist_kernel<<<(unsigned)blocks, 256, hs, st>>>(a.labels, a.n, a.k, a.counts_u);
   ms_scan_kernel<<<1, 1024, 0, st>>>(a.counts_u, a.k, a.offsets, a.cfirst, a.cursor, a.chunks, a.nchunks, a.max_chunks);
-  ms_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.labels, a.n, a.offsets, a.cursor, a.perm);
-  const int R = std::max(1, 256 / a.d);
-  const int threads = R * a.d <= 1024 ? R * a.d : a.d;
-  ms_chunk_sum_kernel<<<(unsigned)a.max_chunks, threads, sizeof(long long) * (size_t)std::max(1, threads / a.d) * a.d, st>>>(
-      a.xa, a.d, a.perm, a.chunks, a.nchunks, a.dc, a.chunk_sums);
+  if (a.k <= kScatterMaxK) {
+    const int64_t sb = (a.n + kScatterPts - 1) / kScatterPts;
+    ms_scatter_block_kernel<<<(unsigned)std::max<int64_t>(1, sb), 256, (size_t)a.k * 12, st>>>(
+        a.labels, a.n, a.k, a.offsets, a.cursor, a.perm);
+  } else {
+    ms_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.labels, a.n, a.offsets, a.cursor, a.perm);
+  }
+  if (a.d % 4 == 0 && a.d <= 1024 &&
+      (reinterpret_cast<uintptr_t>(a.xa) & 15u) == 0) {
+    const int R = std::max(1, 256 / (a.d / 4));
+    const int threads = R * (a.d / 4);
+    ms_chunk_sum4_kernel<<<(unsigned)a.max_chunks, threads, sizeof(long long) * (size_t)R * a.d, st>>>(
+        reinterpret_cast<const float4*>(a.xa), a.d, a.perm, a.chunks, a.nchunks, a.dc, a.chunk_sums);
+  } else {
+    const int R = std::max(1, 256 / a.d);
+    const int threads = R * a.d <= 1024 ? R * a.d : a.d;
+    ms_chunk_sum_kernel<<<(unsigned)a.max_chunks, threads, sizeof(long long) * (size_t)std::max(1, threads / a.d) * a.d,
+                          st>>>(a.xa, a.d, a.perm, a.chunks, a.nchunks, a.dc, a.chunk_sums);
+  }
   ms_finalize_kernel<<<(a.k * a.d + 255) / 256, 256, 0, st>>>(a.counts_u, a.cfirst, a.chunk_sums, a.k, a.d, a.dc,
                                                               a.mu, a.counts, a.df2, a.ls);
   ms_close_kernel<<<1, 1024, 0, st>>>(a.df2, a.k * a.d, a.counts, a.k, a.ls);
