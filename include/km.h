@@ -57,7 +57,7 @@ typedef enum {
   KM_ENOMEM = -2,       /* device or host allocation failed */
   KM_ECUDA = -3,        /* a CUDA call failed, or no usable device */
   KM_ESTATE = -4,       /* step/run before km_set_points and km_set_init */
-  KM_ETIMEOUT = -5,     /* reserved: a bounded device wait gave up */
+  KM_ETIMEOUT = -5,     /* a bounded device wait gave up (error word 3) */
   KM_ENUMERIC = -6      /* NaN/Inf in the points or centroids, or data out of range */
 } km_status;
 
@@ -358,6 +358,16 @@ km_status km_init_learned(km_ctx* ctx, km_setnet* net, int32_t sample_n, uint64_
 
 /* Library version string and the sm architecture it was built for. */
 const char* km_version(void);
+
+/* Self-test of the bounded device waits that every kernel waiting on an
+ * mbarrier uses (the tensor-core path's producer and epilogue): one block
+ * waits on an mbarrier that nothing arrives on, gives up after its limit
+ * (about one second of GPU time) and records that, as a real wait would by
+ * setting the device error word (which the host then reports as
+ * KM_ETIMEOUT).  Sets *gave_up to 1 when the wait ended by its limit and
+ * *elapsed_ms to the wall time of the call; the device stays usable.
+ * Errors: KM_EINVAL (null output), KM_ENOMEM, KM_ECUDA. */
+km_status km_selftest_bounded_wait(int32_t* gave_up, double* elapsed_ms);
 
 #ifdef __cplusplus
 }

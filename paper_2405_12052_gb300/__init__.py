@@ -151,6 +151,8 @@ def lib(path: str | None = None):
     L.km_setnet_last_error.restype = ctypes.c_char_p
     L.km_setnet_destroy.argtypes = [P]
     L.km_setnet_destroy.restype = None
+    L.km_selftest_bounded_wait.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(f64)]
+    L.km_selftest_bounded_wait.restype = st
     L.km_write_labels.argtypes = [P]
     L.km_write_labels.restype = st
     L.km_objective.argtypes = [P, ctypes.POINTER(f64)]
@@ -178,6 +180,16 @@ def lib(path: str | None = None):
     if path is None:
         _lib = L
     return L
+
+
+def selftest_bounded_wait() -> dict:
+    """Run the device-side bounded-wait self-test (a wait on an mbarrier that
+    nothing arrives on must give up by its limit)."""
+    g, ms = ctypes.c_int32(), ctypes.c_double()
+    s = lib().km_selftest_bounded_wait(ctypes.byref(g), ctypes.byref(ms))
+    if s != 0:
+        raise KMError(s, "bounded-wait self-test failed")
+    return {"gave_up": bool(g.value), "elapsed_ms": ms.value}
 
 
 def header_symbols(header: str = HEADER) -> list[str]:

@@ -2,6 +2,7 @@
 // launches of the assign and update kernels, and the loop drivers (one host
 // round trip per step, or a CUDA graph of unrolled steps whose kernels stop
 // themselves once the device-side stop flag is set).
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -9,6 +10,7 @@
 #include <vector>
 
 #include "../../include/km.h"
+
 #include "km_internal.cuh"
 
 using namespace km;
@@ -222,6 +224,8 @@ km_status write_control(km_ctx* c, int done, int max_iter_abs, double tol) {
 km_status read_state(km_ctx* c) {
   KM_CUDA(c, cudaMemcpyAsync(&c->host_ls, c->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, c->st));
   KM_CUDA(c, cudaStreamSynchronize(c->st));
+  if (c->host_ls.error == 3)
+    return fail(c, KM_ETIMEOUT, "a bounded device wait gave up (error word 3)");
   if (c->host_ls.error)
     return fail(c, KM_ECUDA, "device error word set (" + std::to_string(c->host_ls.error) + ")");
   return KM_OK;
@@ -250,6 +254,26 @@ void km_default_options(km_options* opt) {
 }
 
 const char* km_version(void) { return "libkm 0.1 (sm_103a)"; }
+
+km_status km_selftest_bounded_wait(int32_t* gave_up, double* elapsed_ms) {
+  if (!gave_up || !elapsed_ms) return KM_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  int* d = nullptr;
+  cudaStream_t st = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return KM_ENOMEM;
+  int h = -1;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0xFF, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_wait_selftest(d, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return KM_ECUDA;
+  *gave_up = h;
+  *elapsed_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return KM_OK;
+}
 
 km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_options* opt) {
   if (!out) return KM_EINVAL;

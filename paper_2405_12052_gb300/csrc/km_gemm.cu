@@ -873,7 +873,22 @@ __global__ void __launch_bounds__(256) gemm_consts_kernel(GemmPrepArgs a) {
   }
 }
 
+// One thread waits on an mbarrier (expected count 1) that nothing arrives
+// on: wait_bar gives up by its limit, and out[0] = 1 records it.
+__global__ void wait_selftest_kernel(int* out) {
+  __shared__ unsigned long long s_b;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&s_b);
+  bar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  out[0] = wait_bar(b, 0) ? 0 : 1;
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(int* out, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 1, 0, st>>>(out);
+  return cudaGetLastError();
+}
 
 size_t gemm_smem_bytes(int kpad) {
   return 1024 + (size_t)kOffOperands + (size_t)kpad * 128 + 2 * kTileBytes + (size_t)kpad * 4;
