@@ -276,6 +276,12 @@ km_status km_batch_set_init(km_batch* b, const double* mu0);
  * iteration counts unchanged.  Outputs may be NULL. */
 km_status km_batch_tune(km_batch* b, int32_t* tile_out, int32_t* threads_out);
 
+/* Use a launch shape without timing (one the tuner times: tile_points 512 or
+ * 1024, threads 128, 256 or 512), e.g. a shape a previous km_batch_tune chose
+ * for the same instances, kept in a cache.  Errors: KM_EINVAL (another
+ * shape), KM_ESTATE (no points). */
+km_status km_batch_set_shape(km_batch* b, int32_t tile_points, int32_t threads);
+
 /* Run every instance until its selected error is < tol or max_iter more
  * steps have run; the steps are replayed from a captured CUDA graph (4 steps
  * per launch; stopped instances do no work) until no instance is active.
@@ -368,6 +374,13 @@ const char* km_version(void);
  * *elapsed_ms to the wall time of the call; the device stays usable.
  * Errors: KM_EINVAL (null output), KM_ENOMEM, KM_ECUDA. */
 km_status km_selftest_bounded_wait(int32_t* gave_up, double* elapsed_ms);
+
+/* Testing hook (allocation-failure injection, process-wide): after n more
+ * successful device allocations by the library, the next one fails as if
+ * the device were out of memory, and the call making it returns KM_ENOMEM
+ * (the context then only accepts km_destroy, which frees what was
+ * allocated).  n < 0 turns the injection off (the default). */
+void km_debug_fail_alloc_after(int64_t n);
 
 #ifdef __cplusplus
 }

@@ -151,6 +151,8 @@ def lib(path: str | None = None):
     L.km_setnet_last_error.restype = ctypes.c_char_p
     L.km_setnet_destroy.argtypes = [P]
     L.km_setnet_destroy.restype = None
+    L.km_debug_fail_alloc_after.argtypes = [i64]
+    L.km_debug_fail_alloc_after.restype = None
     L.km_selftest_bounded_wait.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(f64)]
     L.km_selftest_bounded_wait.restype = st
     L.km_write_labels.argtypes = [P]
@@ -165,6 +167,8 @@ def lib(path: str | None = None):
     L.km_batch_set_points.restype = st
     L.km_batch_set_init.argtypes = [P, P]
     L.km_batch_set_init.restype = st
+    L.km_batch_set_shape.argtypes = [P, i32, i32]
+    L.km_batch_set_shape.restype = st
     L.km_batch_tune.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.km_batch_tune.restype = st
     L.km_batch_run.argtypes = [P, i32, f64, P, P, P, P, P]
@@ -192,11 +196,25 @@ def selftest_bounded_wait() -> dict:
     return {"gave_up": bool(g.value), "elapsed_ms": ms.value}
 
 
+def debug_fail_alloc_after(n: int):
+    """Testing hook: after n more device allocations by the library, the next
+    one fails as out of memory (n < 0: off)."""
+    lib().km_debug_fail_alloc_after(int(n))
+
+
 def header_symbols(header: str = HEADER) -> list[str]:
     """Names of the functions km.h declares."""
     text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(km_[a-z0-9_]+)\s*\(", text)))
+
+
+def _device_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(torch.cuda.current_device())
+    except Exception:
+        return "unknown"
 
 
 def _is_torch(t) -> bool:
@@ -224,6 +242,7 @@ class KMeans:
         opt = _Options()
         self._L.km_default_options(ctypes.byref(opt))
         opt.e_mode = E_MODES[e_mode]
+        self._e_mode = opt.e_mode
         opt.label_policy = LABEL_POLICIES[label_policy]
         opt.dist_path = DIST_PATHS[dist_path]
         opt.tc_operands = TC_OPERANDS[tc_operands]
@@ -348,6 +367,36 @@ class KMeans:
                                        mu.ctypes.data, ctypes.byref(it), ctypes.byref(e)))
         return dict(labels=labels, centroids=mu, iters=it.value, E=e.value,
                     converged=(s == KM_OK))
+
+    def run_logged(self, max_iter: int, tol: float, objective: bool = False, log=None) -> dict:
+        """Lloyd's loop one step per host round trip, with one record per
+        step (t, E, E^2, empty clusters, points re-checked and decided in
+        FP64, wall ms, evaluations/s, and the objective of the step's labels
+        when asked: one more pass).  Same stopping rule and results as run();
+        ``log`` receives each record as a JSON line."""
+        import json
+        import time
+        squared = self._e_mode == E_MODES["squared"]
+        recs = []
+        converged = False
+        for t in range(1, int(max_iter) + 1):
+            t0 = time.perf_counter()
+            e, e2 = self.step()
+            ms = 1e3 * (time.perf_counter() - t0)
+            st = self.stats()
+            rec = {"t": t, "E": e, "E2": e2, "empty": st["empty_clusters"], "flagged": st["flagged"],
+                   "fp64_decided": st["fp64_decided"], "ms": ms,
+                   "evals_per_s": self.n * self.k / (ms / 1e3) if ms > 0 else None}
+            if objective:
+                rec["objective"] = self.objective()
+            recs.append(rec)
+            if log is not None:
+                log(json.dumps(rec))
+            if (e2 if squared else e) < tol:
+                converged = True
+                break
+        return dict(iters=len(recs), E=recs[-1]["E"] if recs else None, converged=converged,
+                    centroids=self.centroids(), records=recs)
 
     # -- asynchronous pieces of a step (no synchronization) ---------------
     def begin(self, max_iter: int, tol: float):
@@ -482,9 +531,43 @@ class KMeansBatch:
             raise ValueError("flat centroids of the wrong size")
         self._check(self._L.km_batch_set_init(self._h, flat.ctypes.data))
 
-    def tune(self) -> tuple[int, int]:
+    def tune(self, cache: str | None = None) -> tuple[int, int]:
+        """Time the launch shapes and keep the fastest.  With a cache file
+        (``cache`` or the KM_TUNE_CACHE environment variable), a shape chosen
+        before for the same device and the same instance sizes is reused
+        without timing, and a new choice is added to the file."""
+        path = cache if cache is not None else os.environ.get("KM_TUNE_CACHE")
+        key = None
+        if path:
+            import hashlib
+            import json
+            h = hashlib.sha256()
+            h.update(_device_name().encode())
+            for a in (self.n, self.d, self.k):
+                h.update(np.ascontiguousarray(a).tobytes())
+            key = h.hexdigest()[:32]
+            try:
+                with open(path) as f:
+                    hit = json.load(f).get(key)
+            except (OSError, ValueError):
+                hit = None
+            if hit:
+                self._check(self._L.km_batch_set_shape(self._h, int(hit[0]), int(hit[1])))
+                return int(hit[0]), int(hit[1])
         t, th = ctypes.c_int32(), ctypes.c_int32()
         self._check(self._L.km_batch_tune(self._h, ctypes.byref(t), ctypes.byref(th)))
+        if key:
+            import json
+            try:
+                with open(path) as f:
+                    db = json.load(f)
+            except (OSError, ValueError):
+                db = {}
+            db[key] = [t.value, th.value]
+            tmp = f"{path}.tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(db, f)
+            os.replace(tmp, path)
         return t.value, th.value
 
     def run(self, max_iter: int, tol: float, want_labels: bool = True) -> dict:

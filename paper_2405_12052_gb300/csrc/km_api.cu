@@ -2,6 +2,7 @@
 // launches of the assign and update kernels, and the loop drivers (one host
 // round trip per step, or a CUDA graph of unrolled steps whose kernels stop
 // themselves once the device-side stop flag is set).
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -14,6 +15,18 @@
 #include "km_internal.cuh"
 
 using namespace km;
+
+namespace km {
+// allocations left before the injected failure (< 0: off)
+static std::atomic<long long> g_alloc_countdown{-1};
+bool inject_alloc_failure() {
+  long long v = g_alloc_countdown.load();
+  while (v >= 0) {
+    if (g_alloc_countdown.compare_exchange_weak(v, v - 1)) return v == 0;
+  }
+  return false;
+}
+}  // namespace km
 
 struct km_ctx {
   int64_t n = 0;
@@ -100,6 +113,7 @@ km_status fail(km_ctx* c, km_status s, const std::string& msg) {
 
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
+  if (inject_alloc_failure()) return cudaErrorMemoryAllocation;
   return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
 }
 
@@ -254,6 +268,8 @@ void km_default_options(km_options* opt) {
 }
 
 const char* km_version(void) { return "libkm 0.1 (sm_103a)"; }
+
+void km_debug_fail_alloc_after(int64_t n) { g_alloc_countdown.store(n < 0 ? -1 : n); }
 
 km_status km_selftest_bounded_wait(int32_t* gave_up, double* elapsed_ms) {
   if (!gave_up || !elapsed_ms) return KM_EINVAL;

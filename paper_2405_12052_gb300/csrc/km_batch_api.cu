@@ -61,11 +61,14 @@ km_status bfail(km_batch* b, km_status s, const std::string& m) {
 #define KB_CUDA(b, call)                                                                           \
   do {                                                                                             \
     cudaError_t e_ = (call);                                                                       \
-    if (e_ != cudaSuccess) return bfail(b, KM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    if (e_ != cudaSuccess)                                                                         \
+      return bfail(b, e_ == cudaErrorMemoryAllocation ? KM_ENOMEM : KM_ECUDA,                      \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                            \
   } while (0)
 
 template <typename T>
 cudaError_t balloc(T** p, size_t n) {
+  if (inject_alloc_failure()) return cudaErrorMemoryAllocation;
   return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n > 0 ? n : 1));
 }
 
@@ -265,6 +268,23 @@ km_status km_batch_tune(km_batch* b, int32_t* tile_out, int32_t* threads_out) {
   drop_graph(b);
   if (tile_out) *tile_out = bt;
   if (threads_out) *threads_out = bth;
+  return KM_OK;
+}
+
+km_status km_batch_set_shape(km_batch* b, int32_t tile_points, int32_t threads) {
+  if (!b) return KM_EINVAL;
+  if (!b->have_points) return bfail(b, KM_ESTATE, "set_points first");
+  bool ok_t = false, ok_th = false;
+  for (int tp : kTileCand) ok_t = ok_t || tp == tile_points;
+  for (int th : kThreadCand) ok_th = ok_th || th == threads;
+  if (!ok_t || !ok_th) return bfail(b, KM_EINVAL, "tile_points or threads is not one the tuner times");
+  km_status s = build_tiles(b, tile_points);
+  if (s != KM_OK) return s;
+  b->threads = threads;
+  b->grid = grid_for(b, threads);
+  b->tune_ms.clear();
+  b->tuned = true;
+  drop_graph(b);
   return KM_OK;
 }
 

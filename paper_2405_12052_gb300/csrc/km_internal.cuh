@@ -200,6 +200,9 @@ cudaError_t launch_gemm_prep_points(const float* x, int64_t ld, int64_t n, const
                                     float* xaos, int f16, int ex, cudaStream_t st);
 cudaError_t launch_gemm_prepare(cudaStream_t st, const GemmPrepArgs& a);
 cudaError_t launch_wait_selftest(int* out, cudaStream_t st);
+// Allocation-failure injection (testing): true when this device allocation
+// is to fail as if the device were out of memory.
+bool inject_alloc_failure();
 size_t gemm_smem_bytes(int kpad);
 int64_t gemm_xb_rows(int64_t n);
 int64_t msort_max_chunks(int64_t n, int k);

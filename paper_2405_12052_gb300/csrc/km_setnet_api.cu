@@ -35,11 +35,14 @@ km_status nfail(km_setnet* n, km_status s, const std::string& m) {
 #define KN_CUDA(n, call)                                                                           \
   do {                                                                                             \
     cudaError_t e_ = (call);                                                                       \
-    if (e_ != cudaSuccess) return nfail(n, KM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    if (e_ != cudaSuccess)                                                                         \
+      return nfail(n, e_ == cudaErrorMemoryAllocation ? KM_ENOMEM : KM_ECUDA,                      \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                            \
   } while (0)
 
 template <typename T>
 cudaError_t nalloc(T** p, size_t count) {
+  if (inject_alloc_failure()) return cudaErrorMemoryAllocation;
   return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count > 0 ? count : 1));
 }
 

@@ -88,3 +88,30 @@ def test_batch_graph_and_plain_loops_agree_and_resume(km, oracle):
     assert np.array_equal(r3["iters"][late], r1["iters"][late])
     for c in (b1, b2, b3):
         c.close()
+
+
+def test_tuner_cache_reuses_the_shape(km, oracle, tmp_path):
+    """The tuner's choice is kept in a cache file keyed by the device and the
+    instance sizes; a second batch of the same sizes takes it without timing
+    and gives the same results."""
+    insts = [synth.batch_instance(i, n, d, k) for i, (n, d, k) in
+             enumerate([(3000, 2, 5), (12000, 3, 17), (700, 3, 4)])]
+    cache = str(tmp_path / "tune.json")
+    b1 = _batch(km, insts)
+    shape1 = b1.tune(cache=cache)
+    assert len(b1.info()["tune_ms"]) == 6
+    r1 = b1.run(100, 1e-6)
+    b1.close()
+    b2 = _batch(km, insts)
+    shape2 = b2.tune(cache=cache)
+    assert shape2 == shape1 and b2.info()["tune_ms"] == []
+    r2 = b2.run(100, 1e-6)
+    assert np.array_equal(r1["labels"], r2["labels"]) and np.array_equal(r1["centroids"], r2["centroids"])
+    _check_against_oracle(b2, insts, r2, oracle, 100, 1e-6)
+    b2.close()
+    with pytest.raises(km.KMError):
+        b3 = _batch(km, insts)
+        try:
+            b3._check(b3._L.km_batch_set_shape(b3._h, 768, 256))
+        finally:
+            b3.close()

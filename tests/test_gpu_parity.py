@@ -331,3 +331,22 @@ def test_dist_path_option(km, oracle):
     with pytest.raises(km.KMError) as ei:
         km.KMeans(1000, 3, 8, dist_path="tensor")
     assert ei.value.status == -1
+
+
+def test_run_logged_records_every_step(km, oracle):
+    """One record per step; the same stopping step, E and centroids as run()
+    and the oracle; the per-step objective never increases."""
+    w = synth.workload("plain_2d_n1e5_k8")
+    ref = oracle.run(w["x"], w["mu0"], w["max_iter"], w["tol"])
+    g = km.KMeans(w["x"].shape[1], 2, w["k"])
+    g.set_points(w["x"])
+    g.set_init(w["mu0"])
+    lines = []
+    r = g.run_logged(w["max_iter"], w["tol"], objective=True, log=lines.append)
+    assert r["iters"] == ref["iters"] == len(lines) and r["converged"] == ref["converged"]
+    assert abs(r["E"] - ref["E"]) <= E_ABS
+    assert_centroids_close(r["centroids"], ref["centroids"], w["x"])
+    objs = [rec["objective"] for rec in r["records"]]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(objs, objs[1:]))
+    assert [rec["t"] for rec in r["records"]] == list(range(1, r["iters"] + 1))
+    g.close()
