@@ -487,9 +487,11 @@ def run_batch(args, ws, rank, local):
 def run_learned(args, ws, rank, local):
     """Learned initialiser against k-means++ on held-out N = 1e7 anisotropic
     mixtures (K = 16): iterations to tol 1e-6, wall time (start + Lloyd) and
-    final objective of each; the learned result counts only when its
-    objective is within 1e-6 relative of the k-means++ result's (else the
-    fallback's cost is added)."""
+    final objective of each start -- the network on one sample, and the
+    network on 64 rotated copies of the sample with the best converged
+    sample centres (init_multi).  A learned result counts only when its
+    objective is within 1e-6 relative of the k-means++ result's (or lower);
+    otherwise the fallback's cost is added."""
     import numpy as np
     import synth
     count = args.learned_count
@@ -503,32 +505,39 @@ def run_learned(args, ws, rank, local):
     torch.cuda.set_device(local)
     km.build()
     net = learned.load()
-    rows = []
+    variants = {"single": 1, "rotations64": 64}
+    rows = {v: [] for v in variants}
     for s, x in enumerate(xs):
+        xt = torch.from_numpy(x).cuda()
         g = km.KMeans(n, 3, 16)
-        g.set_points(torch.from_numpy(x).cuda(), borrow=True)
+        g.set_points(xt, borrow=True)
         u = np.random.default_rng(700 + s).random(16)
-        for _ in range(2):  # the second pass is the timed one (first builds graphs)
-            r = learned.run_with_fallback(g, net, u, seed=s)
-        rows.append(r)
+        for v, h in variants.items():
+            for _ in range(2):  # the second pass is the timed one (first builds graphs)
+                torch.cuda.synchronize()
+                r = learned.run_with_fallback(g, net, u, seed=s, hypotheses=h, x=xt)
+            rows[v].append(r)
         g.close()
-    ok = [r["objective_learned"] <= r["objective_kpp"] * (1 + 1e-6) for r in rows]
-    wall_l = sum(r["wall_learned"] + (0.0 if o else r["wall_kpp"]) for r, o in zip(rows, ok))
-    wall_k = sum(r["wall_kpp"] for r in rows)
-    it_l = [r["iters_learned"] for r in rows]
-    it_k = [r["iters_kpp"] for r in rows]
+    out_v = {}
+    for v, rs in rows.items():
+        ok = [r["objective_learned"] <= r["objective_kpp"] * (1 + 1e-6) for r in rs]
+        wall_l = sum(r["wall_learned"] + (0.0 if o else r["wall_kpp"]) for r, o in zip(rs, ok))
+        wall_k = sum(r["wall_kpp"] for r in rs)
+        out_v[v] = {"iters_learned": [r["iters_learned"] for r in rs], "iters_kpp": [r["iters_kpp"] for r in rs],
+                    "objective_ratio_learned_over_kpp": [r["objective_learned"] / r["objective_kpp"] for r in rs],
+                    "learned_within_1e-6_or_lower": int(sum(ok)),
+                    "wall_learned_s": sum(r["wall_learned"] for r in rs),
+                    "wall_learned_with_fallback_s": wall_l, "wall_kpp_s": wall_k, "speedup_vs_kpp": wall_k / wall_l}
+    best = out_v["rotations64"]
+    it_l = best["iters_learned"]
     evals = n * 16 * sum(it_l)
-    out = {"metric": METRIC, "value": evals / sum(r["wall_learned"] for r in rows), "unit": UNIT, "n_gpus": 1,
-           "steps": int(sum(it_l)), "warmup": 1, "ms_per_step": 1e3 * sum(r["wall_learned"] for r in rows) / max(1, sum(it_l)),
+    out = {"metric": METRIC, "value": evals / best["wall_learned_s"], "unit": UNIT, "n_gpus": 1,
+           "steps": int(sum(it_l)), "warmup": 1, "ms_per_step": 1e3 * best["wall_learned_s"] / max(1, sum(it_l)),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"learned_init_3d_n{n}_k16", "mixtures": count, "sample": 4096,
-                      "init": "set network vs k-means++ (uniforms seed 700 + s)", "tol": 1e-6, "max_iter": 300,
-                      "parallelism": "single"},
-           "clocks": None, "e2e": None, "gpu_launches": None,
-           "iters_learned": it_l, "iters_kpp": it_k,
-           "objective_ratio_learned_over_kpp": [r["objective_learned"] / r["objective_kpp"] for r in rows],
-           "learned_within_1e-6": int(sum(ok)), "wall_learned_with_fallback_s": wall_l, "wall_kpp_s": wall_k,
-           "speedup_vs_kpp": wall_k / wall_l}
+                      "init": "set network (one sample; 64 rotated samples) vs k-means++ (uniforms seed 700 + s)",
+                      "tol": 1e-6, "max_iter": 300, "parallelism": "single"},
+           "clocks": None, "e2e": None, "gpu_launches": None, "variants": out_v}
     print(json.dumps(out), flush=True)
     return 0
 

@@ -282,6 +282,12 @@ km_status km_batch_tune(km_batch* b, int32_t* tile_out, int32_t* threads_out);
  * shape), KM_ESTATE (no points). */
 km_status km_batch_set_shape(km_batch* b, int32_t tile_points, int32_t threads);
 
+/* Per instance the objective sum_i ||x_i - mu_{z_i}||^2 of its current
+ * labels (last step) and centroids, in FP64 (host out[count]; a fixed
+ * summation order, so repeatable).  Synchronizes.  Errors: KM_EINVAL,
+ * KM_ESTATE, KM_ENOMEM, KM_ECUDA. */
+km_status km_batch_objective(km_batch* b, double* out);
+
 /* Run every instance until its selected error is < tol or max_iter more
  * steps have run; the steps are replayed from a captured CUDA graph (4 steps
  * per launch; stopped instances do no work) until no instance is active.

@@ -167,6 +167,8 @@ def lib(path: str | None = None):
     L.km_batch_set_points.restype = st
     L.km_batch_set_init.argtypes = [P, P]
     L.km_batch_set_init.restype = st
+    L.km_batch_objective.argtypes = [P, P]
+    L.km_batch_objective.restype = st
     L.km_batch_set_shape.argtypes = [P, i32, i32]
     L.km_batch_set_shape.restype = st
     L.km_batch_tune.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -531,6 +533,17 @@ class KMeansBatch:
             raise ValueError("flat centroids of the wrong size")
         self._check(self._L.km_batch_set_init(self._h, flat.ctypes.data))
 
+    def objective(self) -> np.ndarray:
+        """Per instance sum_i ||x_i - mu_{z_i}||^2 of the current labels and
+        centroids (FP64)."""
+        out = np.empty(self.count, dtype=np.float64)
+        self._check(self._L.km_batch_objective(self._h, out.ctypes.data))
+        return out
+
+    def set_shape(self, tile_points: int, threads: int):
+        """Use a launch shape the tuner times, without timing."""
+        self._check(self._L.km_batch_set_shape(self._h, int(tile_points), int(threads)))
+
     def tune(self, cache: str | None = None) -> tuple[int, int]:
         """Time the launch shapes and keep the fastest.  With a cache file
         (``cache`` or the KM_TUNE_CACHE environment variable), a shape chosen
@@ -552,7 +565,7 @@ class KMeansBatch:
             except (OSError, ValueError):
                 hit = None
             if hit:
-                self._check(self._L.km_batch_set_shape(self._h, int(hit[0]), int(hit[1])))
+                self.set_shape(int(hit[0]), int(hit[1]))
                 return int(hit[0]), int(hit[1])
         t, th = ctypes.c_int32(), ctypes.c_int32()
         self._check(self._L.km_batch_tune(self._h, ctypes.byref(t), ctypes.byref(th)))

@@ -417,6 +417,40 @@ cudaError_t launch_batch_update(const BatchArgs& a, int count, cudaStream_t st) 
   return cudaGetLastError();
 }
 
+// Per instance sum_i ||x_i - mu_{z_i}||^2 (current labels and centroids),
+// FP64 without fused multiply-add, one block per instance: thread t takes
+// points t, t + 256, ..., then a fixed-order tree (deterministic).
+__global__ void __launch_bounds__(256) batch_objective_kernel(const float* __restrict__ x,
+                                                              const BatchInst* __restrict__ inst,
+                                                              const int32_t* __restrict__ labels,
+                                                              const double* __restrict__ mu, double* out) {
+  __shared__ double s_red[256];
+  const BatchInst in = inst[blockIdx.x];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < in.n; i += blockDim.x) {
+    const int z = labels[in.lab_off + i];
+    double dd = 0.0;
+    for (int j = 0; j < in.d; ++j) {
+      const double t = __dsub_rn((double)x[in.x_off + (int64_t)j * in.n + i], mu[in.mu_off + z * in.d + j]);
+      dd = __dadd_rn(dd, __dmul_rn(t, t));
+    }
+    acc = __dadd_rn(acc, dd);
+  }
+  s_red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s_red[threadIdx.x] = __dadd_rn(s_red[threadIdx.x], s_red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = s_red[0];
+}
+
+cudaError_t launch_batch_objective(const float* x, const BatchInst* inst, const int32_t* labels, const double* mu,
+                                   double* out, int count, cudaStream_t st) {
+  batch_objective_kernel<<<count, 256, 0, st>>>(x, inst, labels, mu, out);
+  return cudaGetLastError();
+}
+
 int batch_blocks_per_sm(int threads) {
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_assign_kernel, threads, 0) != cudaSuccess) return 1;

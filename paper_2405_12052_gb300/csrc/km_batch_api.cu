@@ -366,6 +366,19 @@ km_status km_batch_get_counts(km_batch* b, int64_t* counts_out) {
   return KM_OK;
 }
 
+km_status km_batch_objective(km_batch* b, double* out) {
+  if (!b || !out) return KM_EINVAL;
+  if (!b->have_points || !b->have_init) return bfail(b, KM_ESTATE, "set_points and set_init first");
+  double* d = nullptr;
+  KB_CUDA(b, balloc(&d, (size_t)b->count));
+  cudaError_t e = launch_batch_objective(b->x, b->inst, b->labels, b->mu, d, b->count, b->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(double) * b->count, cudaMemcpyDeviceToHost, b->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  cudaFree(d);
+  if (e != cudaSuccess) return bfail(b, KM_ECUDA, std::string("objective: ") + cudaGetErrorString(e));
+  return KM_OK;
+}
+
 km_status km_batch_get_info(km_batch* b, km_batch_info* out) {
   if (!b || !out) return KM_EINVAL;
   std::memset(out, 0, sizeof(*out));

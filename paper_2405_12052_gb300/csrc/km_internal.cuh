@@ -257,6 +257,8 @@ cudaError_t launch_batch_tables(const BatchArgs& a, int count, cudaStream_t st);
 cudaError_t launch_batch_assign(const BatchArgs& a, int grid, int threads, cudaStream_t st);
 cudaError_t launch_batch_update(const BatchArgs& a, int count, cudaStream_t st);
 int batch_blocks_per_sm(int threads);
+cudaError_t launch_batch_objective(const float* x, const BatchInst* inst, const int32_t* labels, const double* mu,
+                                   double* out, int count, cudaStream_t st);
 
 // ---- k-means++ seeding ----
 constexpr int kMaxKppD = 256;

@@ -142,13 +142,65 @@ def load(path: str = WEIGHTS) -> SetNet:
     return net
 
 
+def _haar(rng, d: int) -> np.ndarray:
+    """A Haar-distributed rotation (QR of a Gaussian matrix, signs fixed)."""
+    q, r = np.linalg.qr(rng.standard_normal((d, d)))
+    return q * np.sign(np.diag(r))[None, :]
+
+
+def init_multi(g: KMeans, net: SetNet, x, *, hypotheses: int = 64, sample_n: int = 4096, seed: int = 0,
+               max_iter: int = 300, tol: float = 1e-6) -> dict:
+    """Learned start with test-time rotations.  One seeded sample of
+    ``sample_n`` of the points x (d x N, numpy or CUDA tensor; the context's
+    points) is rotated about its mean by the identity and hypotheses - 1
+    seeded Haar rotations; the network predicts K centres for each rotated
+    copy (one batched forward pass) and they are rotated back.  Each
+    prediction starts Lloyd's iteration on the sample (all of them in one
+    batched run), and the converged sample centres with the lowest sample
+    objective become the context's start.  Returns the start and the
+    per-hypothesis sample objectives."""
+    d, n = int(x.shape[0]), int(x.shape[1])
+    k = g.k
+    rng = np.random.Generator(np.random.PCG64(seed))
+    idx = np.sort(rng.choice(n, size=sample_n, replace=False))
+    if hasattr(x, "is_cuda"):
+        import torch
+        xs = x[:, torch.from_numpy(idx).to(x.device)].double().cpu().numpy()
+    else:
+        xs = np.asarray(x)[:, idx].astype(np.float64)
+    m = xs.mean(axis=1, keepdims=True)
+    rots = [np.eye(d)] + [_haar(rng, d) for _ in range(hypotheses - 1)]
+    batch = np.stack([(r @ (xs - m) + m).T for r in rots]).astype(np.float32)   # (H, S, d)
+    pred = net.predict(batch)                                                    # (H, K, d)
+    starts = [(r.T @ (p.T - m) + m).T for r, p in zip(rots, pred)]
+    b = KMeansBatch(np.full(hypotheses, sample_n), np.full(hypotheses, d), np.full(hypotheses, k))
+    try:
+        b.set_points([xs.astype(np.float32)] * hypotheses)
+        b.set_init(starts)
+        b.set_shape(1024, 256)
+        rb = b.run(max_iter, tol, want_labels=False)
+        objs = b.objective()
+        best = int(np.argmin(objs))
+        mu0 = b.split_centroids(rb["centroids"])[best].reshape(k, d)
+    finally:
+        b.close()
+    g.set_init(mu0)
+    return dict(mu0=mu0, hypothesis=best, sample_objectives=objs, sample_iters=rb["iters"])
+
+
 def run_with_fallback(g: KMeans, net: SetNet, uniforms, *, sample_n: int = 4096, seed: int = 0,
-                      max_iter: int = 300, tol: float = 1e-6, judge: bool = True) -> dict:
+                      max_iter: int = 300, tol: float = 1e-6, judge: bool = True, hypotheses: int = 1,
+                      x=None) -> dict:
     """Learned start + Lloyd; with ``judge``, also k-means++ (the given K
     uniforms) + Lloyd, keeping the learned result only if its objective is
-    within 1e-6 relative of the k-means++ result's (else the fallback)."""
+    within 1e-6 relative of the k-means++ result's (else the fallback).
+    hypotheses > 1 takes the rotated-sample start (init_multi; x = the
+    context's points)."""
     t0 = time.perf_counter()
-    g.init_learned(net, sample_n, seed)
+    if hypotheses > 1:
+        init_multi(g, net, x, hypotheses=hypotheses, sample_n=sample_n, seed=seed, max_iter=max_iter, tol=tol)
+    else:
+        g.init_learned(net, sample_n, seed)
     r = g.run(max_iter, tol, want_labels=False)
     obj = g.objective()
     t_learned = time.perf_counter() - t0

@@ -115,3 +115,17 @@ def test_tuner_cache_reuses_the_shape(km, oracle, tmp_path):
             b3._check(b3._L.km_batch_set_shape(b3._h, 768, 256))
         finally:
             b3.close()
+
+
+def test_batch_objective_matches_the_oracle(km, oracle):
+    """Per-instance objective of the final labels and centroids against the
+    oracle's objective of its own final state (FP64, summation orders
+    differ: 1e-12 relative)."""
+    insts = synth.batch_instances(12, seed=21, n_lo=300, n_hi=8_000)
+    b = _batch(km, insts)
+    r = b.run(100, 1e-6)
+    objs = b.objective()
+    for i, w in enumerate(insts):
+        ref = oracle.run(w["x"], w["mu0"], 100, 1e-6)
+        assert abs(objs[i] - ref["objective"]) <= 1e-12 * max(ref["objective"], 1.0), i
+    b.close()

@@ -63,3 +63,36 @@ def test_committed_network_and_fallback(km, oracle):
         report.append({k: v for k, v in r.items() if k != "centroids"})
         g.close()
     print(json.dumps(report))
+
+
+def test_rotated_sample_start(km, oracle):
+    """init_multi: the start is the converged sample centres of the
+    hypothesis with the lowest sample objective (checked against the oracle
+    on the sample), and the judged run never ends above the k-means++
+    objective by more than 1e-6 relative."""
+    import torch
+    from paper_2405_12052_gb300 import learned
+    if not os.path.exists(learned.WEIGHTS):
+        pytest.skip("no committed weights")
+    net = learned.load()
+    x = synth.aniso_mixture(300_000, 3, 16, seed=977)[0]
+    xt = torch.from_numpy(x).cuda()
+    g = km.KMeans(x.shape[1], 3, 16)
+    g.set_points(xt, borrow=True)
+    r = learned.init_multi(g, net, xt, hypotheses=8, seed=3)
+    objs = r["sample_objectives"]
+    assert r["hypothesis"] == int(np.argmin(objs)) and len(objs) == 8
+    # the chosen start is (nearly) a fixed point of Lloyd's iteration on the
+    # sample, and reassigning the sample to it cannot raise its objective
+    idx = np.sort(np.random.Generator(np.random.PCG64(3)).choice(x.shape[1], 4096, replace=False))
+    xs = np.ascontiguousarray(x[:, idx])
+    z = oracle.assign(xs, r["mu0"])
+    assert oracle.objective(xs, r["mu0"], z) <= objs[r["hypothesis"]] * (1 + 1e-9)
+    _, mu1, _, e2 = oracle.step(xs, r["mu0"])
+    assert e2 < 1e-6 * max(1.0, float((r["mu0"] ** 2).sum()))
+    u = np.random.default_rng(5).random(16)
+    rr = learned.run_with_fallback(g, net, u, seed=3, hypotheses=8, x=xt)
+    kept = rr["objective_learned"] if rr["used"] == "learned" else rr["objective_kpp"]
+    assert kept <= rr["objective_kpp"] * (1 + 1e-6)
+    print(json.dumps({k: v for k, v in rr.items() if k != "centroids"}))
+    g.close()
