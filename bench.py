@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--label-policy", default="every_step", choices=["every_step", "final"],
                     help="write the N labels every step, or once after the last step")
+    ap.add_argument("--label-bytes", default="auto", choices=["auto", "4", "1"],
+                    help="label storage: 1 byte (K <= 256, FP32 paths; the default there) or int32")
     ap.add_argument("--tc-operands", default="bf16", choices=["bf16", "f16"],
                     help="operand type of the tensor-core distances (d = 64)")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batch workloads")
@@ -269,7 +271,11 @@ def run_ours(args, ws, rank, local):
     d, n = x.shape
     xt = torch.from_numpy(x).to(dev)
     stream = torch.cuda.current_stream(dev)
-    g = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy, tc_operands=args.tc_operands)
+    lb = 4 if args.label_bytes == "4" else 1
+    if args.label_bytes == "auto" and (k > 256 or d == 64):
+        lb = 4  # 1-byte labels need K <= 256 and the FP32 paths
+    g = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy, tc_operands=args.tc_operands,
+                  label_bytes=lb)
     g.set_points(xt, borrow=True)
     g.set_init(mu0)
     K, W = args.steps, args.warmup
@@ -314,9 +320,10 @@ def run_ours(args, ws, rank, local):
 
     # end to end through the public API with host buffers (pinned)
     xp = torch.from_numpy(x).pin_memory()
-    lab_out = torch.empty(n, dtype=torch.int32).pin_memory()
+    lab_out = torch.empty(n, dtype=torch.uint8 if lb == 1 else torch.int32).pin_memory()
     e2e_times = []
-    g2 = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy, tc_operands=args.tc_operands)
+    g2 = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy, tc_operands=args.tc_operands,
+                   label_bytes=lb)
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -333,7 +340,7 @@ def run_ours(args, ws, rank, local):
     if e2e_times:
         e2e_s = statistics.median(e2e_times)
         e2e = {"value": n * k / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * d * 4 + k * d * 8,
-               "d2h_bytes_per_step": n * 4 + 16}
+               "d2h_bytes_per_step": n * lb + 16}
     else:
         e2e = None
 
@@ -374,7 +381,8 @@ def run_ours(args, ws, rank, local):
                       "l2": "points 1.2 GB > 129 MB L2: no flush needed" if n * d * 4 > 129e6 else "L2-resident",
                       "parallelism": "single" if ws == 1 else f"replicas{ws}",
                       "labels": "one pass after the last step (inside the timed region)" if final_pass
-                                else "written every step"},
+                                else "written every step",
+                      "label_bytes": lb},
            "clocks": clk, "e2e": e2e, "gpu_launches": (11 if stats["path"] == 3 else 2) * K + int(final_pass),
            "roofline": roof,
            "assign_ms": assign_ms, "update_ms": ms_step - assign_ms,

@@ -89,6 +89,10 @@ typedef struct km_options {
                            points and centres scaled by powers of two into FP16's
                            range), so a candidate window 8x narrower; the labels are
                            exact either way */
+  int32_t label_bytes;  /* 4 (default): int32 labels; 1: labels kept as bytes (K <= 256,
+                           FP32 paths only, else KM_EINVAL): a quarter of the label
+                           traffic; read them with km_get_labels_u8 (km_get_labels and
+                           km_run's labels_out still give int32, widened on the device) */
 } km_options;
 
 /* Fill *opt with the defaults above. */
@@ -181,6 +185,9 @@ km_status km_objective(km_ctx* ctx, double* obj_out);
  * pointer of the caller).  Sizes: labels N int32, centroids K x d doubles,
  * counts K int64.  Synchronize the stream. */
 km_status km_get_labels(km_ctx* ctx, int32_t* labels_out, int32_t mem);
+/* The labels as N bytes (contexts created with label_bytes = 1; else
+ * KM_EINVAL).  mem as for km_get_labels.  Synchronizes. */
+km_status km_get_labels_u8(km_ctx* ctx, uint8_t* labels_out, int32_t mem);
 km_status km_get_centroids(km_ctx* ctx, double* centroids_out, int32_t mem);
 km_status km_get_counts(km_ctx* ctx, int64_t* counts_out);
 
@@ -200,7 +207,8 @@ km_status km_get_stats(km_ctx* ctx, km_stats* out);
 
 /* Device pointers owned by the context, for callers that keep data on the
  * GPU (valid until km_destroy).  Points are the SoA copy (or the borrowed
- * pointer) with row stride *ld_out. */
+ * pointer) with row stride *ld_out; *labels is NULL when the context keeps
+ * 1-byte labels. */
 km_status km_device_buffers(km_ctx* ctx, const float** points, int64_t* ld_out,
                             int32_t** labels, double** centroids);
 

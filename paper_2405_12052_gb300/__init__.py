@@ -41,7 +41,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("e_mode", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("tie_rel", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("label_policy", ctypes.c_int32), ("dist_path", ctypes.c_int32),
-                ("tc_operands", ctypes.c_int32)]
+                ("tc_operands", ctypes.c_int32), ("label_bytes", ctypes.c_int32)]
 
 
 LABEL_POLICIES = {"every_step": 0, "final": 1}
@@ -155,6 +155,8 @@ def lib(path: str | None = None):
     L.km_debug_fail_alloc_after.restype = None
     L.km_selftest_bounded_wait.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(f64)]
     L.km_selftest_bounded_wait.restype = st
+    L.km_get_labels_u8.argtypes = [P, P, i32]
+    L.km_get_labels_u8.restype = st
     L.km_write_labels.argtypes = [P]
     L.km_write_labels.restype = st
     L.km_objective.argtypes = [P, ctypes.POINTER(f64)]
@@ -238,7 +240,7 @@ class KMeans:
 
     def __init__(self, n: int, d: int, k: int, *, e_mode: str = "norm", tie_rel: float = 1e-5,
                  use_graph: bool = True, stream=None, label_policy: str = "every_step",
-                 dist_path: str = "auto", tc_operands: str = "bf16"):
+                 dist_path: str = "auto", tc_operands: str = "bf16", label_bytes: int = 4):
         self._L = lib()
         self.n, self.d, self.k = int(n), int(d), int(k)
         opt = _Options()
@@ -248,6 +250,8 @@ class KMeans:
         opt.label_policy = LABEL_POLICIES[label_policy]
         opt.dist_path = DIST_PATHS[dist_path]
         opt.tc_operands = TC_OPERANDS[tc_operands]
+        opt.label_bytes = int(label_bytes)
+        self.label_bytes = int(label_bytes)
         opt.use_graph = 1 if use_graph else 0
         opt.tie_rel = float(tie_rel)
         if stream is None:
@@ -361,12 +365,16 @@ class KMeans:
         return e.value, e2.value
 
     def run(self, max_iter: int, tol: float, want_labels: bool = True) -> dict:
-        labels = np.empty(self.n, dtype=np.int32) if want_labels else None
+        """km_run; labels are int32 (uint8 for a context with 1-byte labels)."""
+        wide = want_labels and self.label_bytes == 4
+        labels = np.empty(self.n, dtype=np.int32) if wide else None
         mu = np.empty((self.k, self.d), dtype=np.float64)
         it, e = ctypes.c_int32(), ctypes.c_double()
         s = self._check(self._L.km_run(self._h, int(max_iter), float(tol),
-                                       labels.ctypes.data if want_labels else None,
+                                       labels.ctypes.data if wide else None,
                                        mu.ctypes.data, ctypes.byref(it), ctypes.byref(e)))
+        if want_labels and not wide:
+            labels = self.labels()
         return dict(labels=labels, centroids=mu, iters=it.value, E=e.value,
                     converged=(s == KM_OK))
 
@@ -420,17 +428,28 @@ class KMeans:
         return int(self._L.km_stream(self._h) or 0)
 
     def labels(self) -> np.ndarray:
+        """The N labels (int32; uint8 for a context with 1-byte labels)."""
+        if self.label_bytes == 1:
+            out8 = np.empty(self.n, dtype=np.uint8)
+            self._check(self._L.km_get_labels_u8(self._h, out8.ctypes.data, KM_HOST))
+            return out8
         out = np.empty(self.n, dtype=np.int32)
         self._check(self._L.km_get_labels(self._h, out.ctypes.data, KM_HOST))
         return out
 
     def labels_host_into(self, tensor):
-        """Copy labels into a host (e.g. pinned) int32 torch tensor of N elements."""
-        self._check(self._L.km_get_labels(self._h, tensor.data_ptr(), KM_HOST))
+        """Copy labels into a host (e.g. pinned) torch tensor of N elements:
+        int32, or uint8 for a context with 1-byte labels (no widening)."""
+        import torch
+        f = self._L.km_get_labels_u8 if tensor.dtype == torch.uint8 else self._L.km_get_labels
+        self._check(f(self._h, tensor.data_ptr(), KM_HOST))
 
     def labels_into(self, tensor):
-        """Copy labels into a CUDA int32 torch tensor of N elements."""
-        self._check(self._L.km_get_labels(self._h, tensor.data_ptr(), KM_DEVICE_COPY))
+        """Copy labels into a CUDA torch tensor of N elements (int32, or uint8
+        for a context with 1-byte labels)."""
+        import torch
+        f = self._L.km_get_labels_u8 if tensor.dtype == torch.uint8 else self._L.km_get_labels
+        self._check(f(self._h, tensor.data_ptr(), KM_DEVICE_COPY))
 
     def centroids(self) -> np.ndarray:
         out = np.empty((self.k, self.d), dtype=np.float64)

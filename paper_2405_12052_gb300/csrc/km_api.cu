@@ -44,6 +44,7 @@ struct km_ctx {
   bool have_points = false, have_init = false;
   // per-step buffers
   int32_t* labels = nullptr;
+  uint8_t* labels8 = nullptr;  // labels as bytes (label_bytes = 1); labels is then not allocated
   double* mu = nullptr;
   long long* counts = nullptr;
   long long* partials = nullptr;
@@ -120,7 +121,7 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_all(km_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
-  void* bufs[] = {c->x_own, c->labels, c->mu, c->counts, c->partials, c->s128, c->tab2,
+  void* bufs[] = {c->x_own, c->labels, c->labels8, c->mu, c->counts, c->partials, c->s128, c->tab2,
                   c->ctil4, c->ctil, c->cnorm, c->shift, c->gen_bmax, c->dc, c->ic, c->ls,
                   c->scan, c->scan_bad, c->xb, c->xa_pt, c->xaos, c->cbf, c->nprime, c->gc,
                   c->ms_counts, c->ms_offsets, c->ms_cfirst, c->ms_cursor, c->ms_chunks, c->ms_nchunks,
@@ -188,7 +189,7 @@ cudaError_t launch_assign(km_ctx* c, bool labels_pass = false) {
     FastArgs a{};
     a.x = c->x; a.ld = c->ld; a.n = c->n; a.k = c->k; a.kpad = c->kpad;
     a.tab2 = c->tab2; a.ctil = c->ctil4; a.mu = c->mu; a.ic = c->ic; a.dc = c->dc;
-    a.ls = c->ls; a.labels = c->labels; a.partials = c->partials;
+    a.ls = c->ls; a.labels = c->labels; a.labels8 = c->labels8; a.partials = c->partials;
     a.ntiles = (c->n + kWarpTile - 1) / kWarpTile;
     a.nwin = c->nwin;
     a.store_labels = store;
@@ -198,7 +199,7 @@ cudaError_t launch_assign(km_ctx* c, bool labels_pass = false) {
     GenericArgs a{};
     a.x = c->x; a.ld = c->ld; a.n = c->n; a.d = c->d; a.k = c->k;
     a.ctil = c->ctil; a.cnorm = c->cnorm; a.mu = c->mu; a.shift = c->shift; a.dc = c->dc;
-    a.ls = c->ls; a.labels = c->labels; a.partials = c->partials;
+    a.ls = c->ls; a.labels = c->labels; a.labels8 = c->labels8; a.partials = c->partials;
     a.A_max = c->A_max; a.B_max_ptr = c->gen_bmax; a.tau = (float)(c->opt.tie_rel * (1.0 + 1e-4));
     a.store_labels = store;
     a.ignore_done = labels_pass ? 1 : 0;
@@ -265,6 +266,7 @@ void km_default_options(km_options* opt) {
   opt->label_policy = KM_LABELS_EVERY_STEP;
   opt->dist_path = KM_DIST_AUTO;
   opt->tc_operands = KM_TC_BF16;
+  opt->label_bytes = 4;
 }
 
 const char* km_version(void) { return "libkm 0.1 (sm_103a)"; }
@@ -309,6 +311,8 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
     return fail(c, KM_EINVAL, "dist_path out of range");
   if (c->opt.tc_operands != KM_TC_BF16 && c->opt.tc_operands != KM_TC_F16)
     return fail(c, KM_EINVAL, "tc_operands out of range");
+  if (c->opt.label_bytes != 4 && c->opt.label_bytes != 1) return fail(c, KM_EINVAL, "label_bytes must be 4 or 1");
+  if (c->opt.label_bytes == 1 && k > 256) return fail(c, KM_EINVAL, "1-byte labels need K <= 256");
   if (c->opt.e_mode != KM_E_NORM && c->opt.e_mode != KM_E_SQUARED) return fail(c, KM_EINVAL, "bad e_mode");
   KM_CUDA(c, cudaGetDevice(&c->dev));
   cudaDeviceProp p{};
@@ -340,6 +344,8 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
   if (c->opt.dist_path == KM_DIST_TENSOR && !gemm)
     return fail(c, KM_EINVAL, "tensor-core distances need d = 64, K <= 1024 and N < 2^31");
   c->path = c->opt.dist_path == KM_DIST_TENSOR ? 3 : (c->fast ? 1 : ((gemm && c->opt.dist_path == KM_DIST_AUTO) ? 3 : 2));
+  if (c->path == 3 && c->opt.label_bytes == 1)
+    return fail(c, KM_EINVAL, "1-byte labels are for the FP32 paths (the tensor-core path reads int32 labels)");
   if (c->path == 3) {
     c->kpad = (k + 255) / 256 * 256;
     c->G = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, c->sms));
@@ -358,7 +364,8 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
   }
   c->RB = (int)std::max<int64_t>(1, std::min<int64_t>(16, (c->G + kWarps * 4 - 1) / (kWarps * 4)));
   const size_t cols = (size_t)k * (d + 1);
-  KM_CUDA(c, dalloc(&c->labels, (size_t)n));
+  if (c->opt.label_bytes == 1) KM_CUDA(c, dalloc(&c->labels8, (size_t)n));
+  else KM_CUDA(c, dalloc(&c->labels, (size_t)n));
   KM_CUDA(c, dalloc(&c->mu, (size_t)k * d));
   KM_CUDA(c, dalloc(&c->counts, (size_t)k));
   KM_CUDA(c, dalloc(&c->partials, (size_t)c->G * cols));
@@ -398,7 +405,8 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
   }
   KM_CUDA(c, cudaMemsetAsync(c->ls, 0, sizeof(LoopState), c->st));
   KM_CUDA(c, cudaMemsetAsync(c->counts, 0, sizeof(long long) * k, c->st));
-  KM_CUDA(c, cudaMemsetAsync(c->labels, 0, sizeof(int32_t) * n, c->st));
+  if (c->labels8) KM_CUDA(c, cudaMemsetAsync(c->labels8, 0, (size_t)n, c->st));
+  else KM_CUDA(c, cudaMemsetAsync(c->labels, 0, sizeof(int32_t) * n, c->st));
   KM_CUDA(c, cudaStreamSynchronize(c->st));
   return KM_OK;
 }
@@ -596,11 +604,33 @@ km_status km_objective(km_ctx* c, double* obj_out) {
   const int64_t nch = objective_chunks(c->n);
   cudaError_t e = dalloc(&part, (size_t)nch + 1);
   if (e != cudaSuccess) return fail(c, KM_ENOMEM, std::string("objective buffer: ") + cudaGetErrorString(e));
-  e = launch_objective(c->x, c->ld, c->n, c->d, c->mu, c->labels, part, part + nch, c->st);
+  e = launch_objective(c->x, c->ld, c->n, c->d, c->mu, c->labels, c->labels8, part, part + nch, c->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(obj_out, part + nch, sizeof(double), cudaMemcpyDeviceToHost, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   cudaFree(part);
   if (e != cudaSuccess) return fail(c, KM_ECUDA, std::string("objective: ") + cudaGetErrorString(e));
+  return KM_OK;
+}
+
+// int32 labels to out (host or device), widening byte labels on the device
+// first (into a temporary buffer for a host destination).  Queued only.
+static km_status copy_labels_i32(km_ctx* c, int32_t* out, int32_t mem) {
+  if (!c->labels8) {
+    KM_CUDA(c, cudaMemcpyAsync(out, c->labels, sizeof(int32_t) * c->n,
+                               mem == KM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st));
+    return KM_OK;
+  }
+  if (mem == KM_DEVICE_COPY) {
+    KM_CUDA(c, launch_widen_labels(c->labels8, out, c->n, c->st));
+    return KM_OK;
+  }
+  int32_t* tmp = nullptr;
+  KM_CUDA(c, dalloc(&tmp, (size_t)c->n));
+  cudaError_t e = launch_widen_labels(c->labels8, tmp, c->n, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return fail(c, KM_ECUDA, std::string("labels: ") + cudaGetErrorString(e));
   return KM_OK;
 }
 
@@ -670,8 +700,10 @@ km_status km_run(km_ctx* c, int32_t max_iter, double tol, int32_t* labels_out,
     s = km_write_labels(c);
     if (s != KM_OK) return s;
   }
-  if (labels_out)
-    KM_CUDA(c, cudaMemcpyAsync(labels_out, c->labels, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st));
+  if (labels_out) {
+    s = copy_labels_i32(c, labels_out, KM_HOST);
+    if (s != KM_OK) return s;
+  }
   if (centroids_out)
     KM_CUDA(c, cudaMemcpyAsync(centroids_out, c->mu, sizeof(double) * c->k * c->d, cudaMemcpyDeviceToHost, c->st));
   KM_CUDA(c, cudaStreamSynchronize(c->st));
@@ -718,7 +750,17 @@ void* km_stream(km_ctx* c) { return c ? (void*)c->st : nullptr; }
 km_status km_get_labels(km_ctx* c, int32_t* out, int32_t mem) {
   if (!c) return KM_EINVAL;
   if (!out || (mem != KM_HOST && mem != KM_DEVICE_COPY)) return fail(c, KM_EINVAL, "bad output");
-  KM_CUDA(c, cudaMemcpyAsync(out, c->labels, sizeof(int32_t) * c->n,
+  km_status s = copy_labels_i32(c, out, mem);
+  if (s != KM_OK) return s;
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  return KM_OK;
+}
+
+km_status km_get_labels_u8(km_ctx* c, uint8_t* out, int32_t mem) {
+  if (!c) return KM_EINVAL;
+  if (!out || (mem != KM_HOST && mem != KM_DEVICE_COPY)) return fail(c, KM_EINVAL, "bad output");
+  if (!c->labels8) return fail(c, KM_EINVAL, "labels are stored as int32 (label_bytes = 4)");
+  KM_CUDA(c, cudaMemcpyAsync(out, c->labels8, (size_t)c->n,
                              mem == KM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st));
   KM_CUDA(c, cudaStreamSynchronize(c->st));
   return KM_OK;

@@ -282,7 +282,10 @@ __device__ void drain_warp_queue(const FastArgs& a, FastSmem<D>& sm, uint32_t* q
       bool used64;
       const int kk = recheck_fast<D>(xo, s, sm.ctil, a.mu, a.k, B_max, tau, used64);
       n64 += used64 ? 1 : 0;
-      if (a.store_labels) a.labels[i] = kk;
+      if (a.store_labels) {
+        if (a.labels8) a.labels8[i] = (uint8_t)kk;
+        else a.labels[i] = kk;
+      }
       accumulate_point<D>(wmine, kk, xo, dc.C_hi, dc.C_lo);
     }
     if ((r & rmask) == rmask) flush_windows<D>(wwarp, acc, a.k, a.nwin, lane, dc.bits_C_hi, dc.bits_C_lo);
@@ -436,7 +439,15 @@ __device__ __forceinline__ void process_tile(const FastArgs& a, FastSmem<D>& sm,
   for (int g = 0; g < kNG; ++g) {
     const int64_t i0 = base + g * kGS + 4 * lane;
     if (!a.store_labels) break;
-    if constexpr (FULL) {
+    if (a.labels8) {
+      if constexpr (FULL) {
+        *reinterpret_cast<uchar4*>(a.labels8 + i0) = make_uchar4((unsigned char)lab[4 * g], (unsigned char)lab[4 * g + 1],
+                                                                 (unsigned char)lab[4 * g + 2], (unsigned char)lab[4 * g + 3]);
+      } else {
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) if (i0 + qq < a.n) a.labels8[i0 + qq] = (uint8_t)lab[4 * g + qq];
+      }
+    } else if constexpr (FULL) {
       *reinterpret_cast<int4*>(a.labels + i0) = make_int4(lab[4 * g], lab[4 * g + 1], lab[4 * g + 2], lab[4 * g + 3]);
     } else {
 #pragma unroll
@@ -624,7 +635,10 @@ __global__ void __launch_bounds__(kThreads) assign_generic_kernel(GenericArgs a)
         }
       }
     }
-    if (a.store_labels) a.labels[i] = kb;
+    if (a.store_labels) {
+      if (a.labels8) a.labels8[i] = (uint8_t)kb;
+      else a.labels[i] = kb;
+    }
     unsigned long long* r = row + (size_t)kb * dp;
     for (int j = 0; j < d; ++j) {
       uint32_t bh, bl;

@@ -113,6 +113,7 @@ struct FastArgs {
   int64_t ntiles;
   int nwin;                        // 32-bit sum windows per warp: 2 (one per half-warp) or 1 (large K)
   int store_labels;                // 0: labels are not written (label policy "final")
+  uint8_t* labels8;                // non-null: labels are written here as bytes (K <= 256), not to labels
   int ignore_done;                 // 1: run even after the stop flag (the final labels pass)
 };
 
@@ -130,6 +131,7 @@ struct GenericArgs {
   const float* B_max_ptr;          // max_k ||c~_k||^2, written by the update kernel
   float tau;
   int store_labels;                // as in FastArgs
+  uint8_t* labels8;                // as in FastArgs
   int ignore_done;
 };
 
@@ -292,8 +294,9 @@ cudaError_t launch_setnet_destandardize(const float* P, const float* ms, int B, 
 
 // ---- objective ----
 int64_t objective_chunks(int64_t n);
+cudaError_t launch_widen_labels(const uint8_t* z8, int32_t* z, int64_t n, cudaStream_t st);
 cudaError_t launch_objective(const float* x, int64_t ld, int64_t n, int d, const double* mu, const int32_t* z,
-                             double* part, double* out, cudaStream_t st);
+                             const uint8_t* z8, double* part, double* out, cudaStream_t st);
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_assign_fast(int d, int grid, size_t smem, cudaStream_t st, const FastArgs& a);

@@ -3,6 +3,8 @@
 // current labels and centroids, in FP64: per point the squared distance with
 // coordinates in order (no fused multiply-add), summed in index order within
 // chunks of 65536 points, the chunk sums then added in chunk order.
+#include <algorithm>
+
 #include "km_internal.cuh"
 
 namespace km {
@@ -13,9 +15,10 @@ constexpr int kObjChunk = 65536;
 
 // One warp per chunk: lanes form 32 distances at a time, lane 0 adds them in
 // index order.
+template <typename L>
 __global__ void __launch_bounds__(256) objective_kernel(const float* __restrict__ x, int64_t ld, int64_t n, int d,
                                                         const double* __restrict__ mu,
-                                                        const int32_t* __restrict__ z, double* part,
+                                                        const L* __restrict__ z, double* part,
                                                         int nchunks) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (w >= nchunks) return;
@@ -46,14 +49,28 @@ __global__ void objective_sum_kernel(const double* part, int nchunks, double* ou
   *out = s;
 }
 
+__global__ void widen_labels_kernel(const uint8_t* __restrict__ z8, int32_t* __restrict__ z, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = z8[i];
+}
+
 }  // namespace
+
+cudaError_t launch_widen_labels(const uint8_t* z8, int32_t* z, int64_t n, cudaStream_t st) {
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192));
+  widen_labels_kernel<<<(unsigned)blocks, 256, 0, st>>>(z8, z, n);
+  return cudaGetLastError();
+}
 
 int64_t objective_chunks(int64_t n) { return (n + kObjChunk - 1) / kObjChunk; }
 
 cudaError_t launch_objective(const float* x, int64_t ld, int64_t n, int d, const double* mu, const int32_t* z,
-                             double* part, double* out, cudaStream_t st) {
+                             const uint8_t* z8, double* part, double* out, cudaStream_t st) {
   const int nch = (int)objective_chunks(n);
-  objective_kernel<<<(nch * 32 + 255) / 256, 256, 0, st>>>(x, ld, n, d, mu, z, part, nch);
+  if (z8)
+    objective_kernel<uint8_t><<<(nch * 32 + 255) / 256, 256, 0, st>>>(x, ld, n, d, mu, z8, part, nch);
+  else
+    objective_kernel<int32_t><<<(nch * 32 + 255) / 256, 256, 0, st>>>(x, ld, n, d, mu, z, part, nch);
   objective_sum_kernel<<<1, 1, 0, st>>>(part, nch, out);
   return cudaGetLastError();
 }

@@ -350,3 +350,51 @@ def test_run_logged_records_every_step(km, oracle):
     assert all(b <= a * (1 + 1e-12) for a, b in zip(objs, objs[1:]))
     assert [rec["t"] for rec in r["records"]] == list(range(1, r["iters"] + 1))
     g.close()
+
+
+@pytest.mark.parametrize("case", ["fused_3d", "fused_k256_offset", "generic_d5"])
+def test_one_byte_labels(km, oracle, case):
+    """label_bytes = 1 (K <= 256): the labels are kept and copied out as
+    bytes, equal to the oracle's; the int32 getter widens them; the
+    objective and a full run agree with the 4-byte context."""
+    if case == "fused_3d":
+        x, _, _ = synth.aniso_mixture(100_003, 3, 12, seed=61)
+        k = 32
+    elif case == "fused_k256_offset":
+        x, _, _ = synth.iso_mixture(80_000, 3, 256, sigma=1.0, box=50.0, seed=62, weights="dirichlet", offset=1e4)
+        k = 256
+    else:
+        x, _, _ = synth.iso_mixture(20_001, 5, 4, seed=63)
+        k = 7
+    mu0, _ = synth.init_distinct(x, k, seed=64)
+    st = lockstep(km, oracle, x, mu0, steps=2, label_bytes=1)
+    assert st["path"] == (2 if case == "generic_d5" else 1)
+    d, n = x.shape
+    out = {}
+    for lb in (4, 1):
+        g = km.KMeans(n, d, k, label_bytes=lb)
+        g.set_points(x)
+        g.set_init(mu0)
+        r = g.run(40, 1e-6)
+        out[lb] = (r, g.objective(), g.labels())
+        if lb == 1:
+            assert out[lb][2].dtype == np.uint8
+            wide = np.empty(n, dtype=np.int32)
+            g._check(g._L.km_get_labels(g._h, wide.ctypes.data, 0))
+            assert np.array_equal(wide, out[lb][2])
+        g.close()
+    (r4, o4, z4), (r1, o1, z1) = out[4], out[1]
+    assert r4["iters"] == r1["iters"] and np.array_equal(r4["centroids"], r1["centroids"]) and o4 == o1
+    assert np.array_equal(z4, z1) and np.array_equal(r4["labels"], r1["labels"])
+
+
+def test_one_byte_labels_limits(km):
+    with pytest.raises(km.KMError) as ei:
+        km.KMeans(1000, 3, 257, label_bytes=1)
+    assert ei.value.status == -1
+    with pytest.raises(km.KMError) as ei:
+        km.KMeans(1000, 64, 16, label_bytes=1)   # the tensor-core path reads int32 labels
+    assert ei.value.status == -1
+    g = km.KMeans(1000, 64, 16, label_bytes=1, dist_path="simt")
+    assert g.stats()["path"] == 2
+    g.close()
