@@ -331,14 +331,15 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
   const bool gemm = d == kGemmD && k <= kGemmMaxK && n < (int64_t(1) << 31) &&
                     gemm_smem_bytes((k + 255) / 256 * 256) <= (size_t)p.sharedMemPerBlockOptin;
   if (c->fast) {
-    // one 32-bit sum window per half-warp when it fits, else one per warp
-    c->nwin = 2;
-    c->fast_smem = fast_smem_bytes(d, c->kpad, k, 2);
-    if (c->fast_smem > (size_t)p.sharedMemPerBlockOptin) {
-      c->nwin = 1;
-      c->fast_smem = fast_smem_bytes(d, c->kpad, k, 1);
-    }
-    if (c->fast_smem > (size_t)p.sharedMemPerBlockOptin) c->fast = false;
+    // one 32-bit sum window per half-warp (double-buffered points) when it
+    // fits with as many resident blocks per SM as one window per warp
+    // (single-buffered points) allows, else the smaller layout
+    const size_t s2 = fast_smem_bytes(d, c->kpad, k, 2), s1 = fast_smem_bytes(d, c->kpad, k, 1);
+    const size_t lim = (size_t)p.sharedMemPerBlockOptin;
+    const int b2 = s2 <= lim ? fast_blocks_per_sm(d, s2) : 0, b1 = s1 <= lim ? fast_blocks_per_sm(d, s1) : 0;
+    c->nwin = (b2 > 0 && b2 >= b1) ? 2 : 1;
+    c->fast_smem = c->nwin == 2 ? s2 : s1;
+    if (c->fast_smem > lim || (c->nwin == 1 ? b1 : b2) == 0) c->fast = false;
   }
   const int64_t ntiles = (n + kWarpTile - 1) / kWarpTile;  // warp-tiles of 256 points
   if (c->opt.dist_path == KM_DIST_TENSOR && !gemm)

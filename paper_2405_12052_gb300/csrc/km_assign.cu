@@ -183,33 +183,33 @@ __device__ __forceinline__ void top2_one(float& m1, float& m2, float v) {
   m2 = fminf(m2, t);
 }
 
-// Shared memory of the fused kernel.  Everything but the tables is private
-// to one warp: warps never wait for each other until the end.
+// Shared memory of the fused kernel.  The windows, point buffers and queues
+// are private to one warp; the int64 totals are the block's (windows are
+// flushed into them with 64-bit shared atomics).  With one window per warp
+// (large K) the points are single-buffered, so that two blocks fit on an SM.
 template <int D>
 struct FastSmem {
   static constexpr int DP = D + 1, WIN = 2 * D + 1;
   static constexpr int GS = (DP & 1) ? DP : DP + 1;  // float4 slots per group (odd: no bank conflicts)
   unsigned long long* tab;  // [kpad][DP] screen table, packed (a, a) pairs (block)
-  long long* acc;           // [kWarps][k][DP] int64 totals
-  float4* ctil;             // [k] fp32 centroids for the re-check (block)
+  long long* acc;           // [k][DP] int64 totals (block)
   float4* gtab;             // [kpad/4][GS] screen table by group: slot j = coefficient j of the 4 centroids
-  float* xbuf;              // [kWarps][2][D][kWarpTile] double-buffered points
+  float* xbuf;              // [kWarps][nbuf][D][kWarpTile] points (double-buffered when nbuf = 2)
   uint32_t* queue;          // [kWarps][kWarpQueue] flagged points
   uint32_t* win;            // [kWarps][nwin][k+1][WIN] 32-bit windows (per half-warp when nwin = 2); bin k discards
   int* cnt;                 // [2]: flagged, fp64-decided (block totals)
-  __device__ FastSmem(unsigned char* sm, int kpad, int k, int nwin) {
+  __device__ FastSmem(unsigned char* sm, int kpad, int k, int nwin, int nbuf) {
     tab = reinterpret_cast<unsigned long long*>(sm);
     acc = reinterpret_cast<long long*>(tab + (size_t)kpad * DP);
-    ctil = reinterpret_cast<float4*>(acc + (size_t)kWarps * k * DP);
-    gtab = ctil + k;
+    gtab = reinterpret_cast<float4*>(acc + (size_t)k * DP + (k * DP & 1));
     xbuf = reinterpret_cast<float*>(gtab + (size_t)(kpad / 4) * GS);
-    queue = reinterpret_cast<uint32_t*>(xbuf + (size_t)kWarps * 2 * D * kWarpTile);
+    queue = reinterpret_cast<uint32_t*>(xbuf + (size_t)kWarps * nbuf * D * kWarpTile);
     win = queue + (size_t)kWarps * kWarpQueue;
     cnt = reinterpret_cast<int*>(win + (size_t)kWarps * nwin * (k + 1) * WIN);
   }
 };
 
-// Flush the warp's windows (nwin of them) into its int64 totals.  acc
+// Flush the warp's windows (nwin of them) into the block's int64 totals.  acc
 // columns per centroid: 0..D-1 coordinate sums, D the count (the layout of
 // the per-block partials); window slots: 0 the count, 1..D the high limbs,
 // D+1..2D the low limbs.
@@ -233,7 +233,7 @@ __device__ __forceinline__ void flush_windows(uint32_t* wwarp, long long* acc, i
         v += ((long long)hi << 22) + (long long)lo;
       }
     }
-    acc[s] += v;
+    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&acc[s]), (unsigned long long)v);
   }
   __syncwarp();
   for (int s = lane; s < nwin * half; s += 32) wwarp[s] = 0u;
@@ -280,7 +280,7 @@ __device__ void drain_warp_queue(const FastArgs& a, FastSmem<D>& sm, uint32_t* q
 #pragma unroll
       for (int j = 0; j < D; ++j) xo[j] = a.x[(int64_t)j * a.ld + i];
       bool used64;
-      const int kk = recheck_fast<D>(xo, s, sm.ctil, a.mu, a.k, B_max, tau, used64);
+      const int kk = recheck_fast<D>(xo, s, a.ctil, a.mu, a.k, B_max, tau, used64);
       n64 += used64 ? 1 : 0;
       if (a.store_labels) {
         if (a.labels8) a.labels8[i] = (uint8_t)kk;
@@ -492,7 +492,8 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
   constexpr int DP = D + 1, WIN = 2 * D + 1, GS = FastSmem<D>::GS;
   extern __shared__ __align__(16) unsigned char smraw[];
   if (a.ls->done && !a.ignore_done) return;  // the loop already stopped (graph-driven runs)
-  FastSmem<D> sm(smraw, a.kpad, a.k, a.nwin);
+  const int nbuf = a.nwin == 1 ? 1 : 2;
+  FastSmem<D> sm(smraw, a.kpad, a.k, a.nwin, nbuf);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = a.k, kpad = a.kpad;
 
@@ -506,9 +507,9 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
   const int nwin = a.nwin;
   uint32_t* wwarp = sm.win + (size_t)warp * nwin * (k + 1) * WIN;
   uint32_t* wmine = wwarp + (size_t)(nwin == 2 ? (lane >> 4) : 0) * (k + 1) * WIN;
-  long long* acc = sm.acc + (size_t)warp * k * DP;
+  long long* acc = sm.acc;
   uint32_t* q = sm.queue + (size_t)warp * kWarpQueue;
-  float* xb = sm.xbuf + (size_t)warp * 2 * D * kWarpTile;
+  float* xb = sm.xbuf + (size_t)warp * nbuf * D * kWarpTile;
   const int wid = blockIdx.x * kWarps + warp;  // this warp's first tile
   const int wtot = gridDim.x * kWarps;         // tile stride
   const int ntiles = (int)a.ntiles;            // < 2^31 (N < 2^39)
@@ -520,8 +521,7 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
     const int c = q2 / DP, j = q2 - c * DP;
     reinterpret_cast<float*>(sm.gtab + (size_t)(c >> 2) * GS + j)[c & 3] = __uint_as_float((uint32_t)v);
   }
-  for (int q2 = tid; q2 < k; q2 += kThreads) sm.ctil[q2] = a.ctil[q2];
-  for (int q2 = tid; q2 < kWarps * k * DP; q2 += kThreads) sm.acc[q2] = 0;
+  for (int q2 = tid; q2 < k * DP; q2 += kThreads) sm.acc[q2] = 0;
   for (int q2 = tid; q2 < kWarps * nwin * (k + 1) * WIN; q2 += kThreads) sm.win[q2] = 0u;
   if (tid < 2) sm.cnt[tid] = 0;
   __syncthreads();
@@ -536,14 +536,17 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
 
   for (int tile = wid; tile < ntiles; tile += wtot, ++m) {
     const int64_t base = (int64_t)tile * kWarpTile;
-    const float* xcur = xb + (m & 1) * D * kWarpTile;
+    const float* xcur = xb + (nbuf == 2 ? (m & 1) : 0) * D * kWarpTile;
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (tile + wtot < ntiles)
+    // each lane reads only the chunks it copied itself, so the next copy
+    // needs no warp barrier
+    if (nbuf == 2 && tile + wtot < ntiles)
       prefetch_tile<D>(a, xb + ((m + 1) & 1) * D * kWarpTile, (int64_t)(tile + wtot) * kWarpTile, lane);
     if (base + kWarpTile <= a.n)
       process_tile<D, true>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
     else
       process_tile<D, false>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
+    if (nbuf == 1 && tile + wtot < ntiles) prefetch_tile<D>(a, xb, (int64_t)(tile + wtot) * kWarpTile, lane);
     // 16 lanes x 8 points x 4 tiles (or 32 lanes x 8 points x 2 tiles): <= 512 additions per bin
     if (++since_flush == (nwin == 2 ? 4 : 2)) {
       flush_windows<D>(wwarp, acc, k, nwin, lane, dc.bits_C_hi, dc.bits_C_lo);
@@ -569,12 +572,7 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
   if (n64) atomicAdd(&sm.cnt[1], n64);
   __syncthreads();
   long long* out = a.partials + (size_t)blockIdx.x * k * DP;
-  for (int q2 = tid; q2 < k * DP; q2 += kThreads) {
-    long long v = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) v += sm.acc[(size_t)w * k * DP + q2];
-    out[q2] = v;
-  }
+  for (int q2 = tid; q2 < k * DP; q2 += kThreads) out[q2] = sm.acc[q2];
   if (tid == 0) {
     if (sm.cnt[0]) atomicAdd(&a.ls->flagged, (unsigned long long)sm.cnt[0]);
     if (sm.cnt[1]) atomicAdd(&a.ls->fp64_decided, (unsigned long long)sm.cnt[1]);
@@ -661,8 +659,9 @@ __global__ void __launch_bounds__(kThreads) assign_generic_kernel(GenericArgs a)
 
 size_t fast_smem_bytes(int d, int kpad, int k, int nwin) {
   const int dp = d + 1, win = 2 * d + 1, gs = (dp & 1) ? dp : dp + 1;
-  size_t b = (size_t)kpad * dp * 8 + (size_t)kWarps * k * dp * 8 + (size_t)k * 16 + (size_t)(kpad / 4) * gs * 16 +
-             (size_t)kWarps * 2 * d * kWarpTile * 4 + (size_t)kWarps * kWarpQueue * 4 +
+  const int nbuf = nwin == 1 ? 1 : 2;
+  size_t b = (size_t)kpad * dp * 8 + (size_t)(k * dp + (k * dp & 1)) * 8 + (size_t)(kpad / 4) * gs * 16 +
+             (size_t)kWarps * nbuf * d * kWarpTile * 4 + (size_t)kWarps * kWarpQueue * 4 +
              (size_t)kWarps * nwin * (k + 1) * win * 4 + 16;
   return (b + 15) & ~size_t(15);
 }
