@@ -194,6 +194,7 @@ struct FastSmem {
   unsigned long long* tab;  // [kpad][DP] screen table, packed (a, a) pairs (block)
   long long* acc;           // [k][DP] int64 totals (block)
   float4* gtab;             // [kpad/4][GS] screen table by group: slot j = coefficient j of the 4 centroids
+  float4* ctil;             // [k] fp32 centroids for the re-check (block; two-window layout only, else global)
   float* xbuf;              // [kWarps][nbuf][D][kWarpTile] points (double-buffered when nbuf = 2)
   uint32_t* queue;          // [kWarps][kWarpQueue] flagged points
   uint32_t* win;            // [kWarps][nwin][k+1][WIN] 32-bit windows (per half-warp when nwin = 2); bin k discards
@@ -202,7 +203,8 @@ struct FastSmem {
     tab = reinterpret_cast<unsigned long long*>(sm);
     acc = reinterpret_cast<long long*>(tab + (size_t)kpad * DP);
     gtab = reinterpret_cast<float4*>(acc + (size_t)k * DP + (k * DP & 1));
-    xbuf = reinterpret_cast<float*>(gtab + (size_t)(kpad / 4) * GS);
+    ctil = nbuf == 2 ? gtab + (size_t)(kpad / 4) * GS : nullptr;
+    xbuf = reinterpret_cast<float*>(gtab + (size_t)(kpad / 4) * GS + (nbuf == 2 ? k : 0));
     queue = reinterpret_cast<uint32_t*>(xbuf + (size_t)kWarps * nbuf * D * kWarpTile);
     win = queue + (size_t)kWarps * kWarpQueue;
     cnt = reinterpret_cast<int*>(win + (size_t)kWarps * nwin * (k + 1) * WIN);
@@ -280,7 +282,7 @@ __device__ void drain_warp_queue(const FastArgs& a, FastSmem<D>& sm, uint32_t* q
 #pragma unroll
       for (int j = 0; j < D; ++j) xo[j] = a.x[(int64_t)j * a.ld + i];
       bool used64;
-      const int kk = recheck_fast<D>(xo, s, a.ctil, a.mu, a.k, B_max, tau, used64);
+      const int kk = recheck_fast<D>(xo, s, sm.ctil ? sm.ctil : a.ctil, a.mu, a.k, B_max, tau, used64);
       n64 += used64 ? 1 : 0;
       if (a.store_labels) {
         if (a.labels8) a.labels8[i] = (uint8_t)kk;
@@ -522,6 +524,8 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
     reinterpret_cast<float*>(sm.gtab + (size_t)(c >> 2) * GS + j)[c & 3] = __uint_as_float((uint32_t)v);
   }
   for (int q2 = tid; q2 < k * DP; q2 += kThreads) sm.acc[q2] = 0;
+  if (sm.ctil)
+    for (int q2 = tid; q2 < k; q2 += kThreads) sm.ctil[q2] = a.ctil[q2];
   for (int q2 = tid; q2 < kWarps * nwin * (k + 1) * WIN; q2 += kThreads) sm.win[q2] = 0u;
   if (tid < 2) sm.cnt[tid] = 0;
   __syncthreads();
@@ -661,6 +665,7 @@ size_t fast_smem_bytes(int d, int kpad, int k, int nwin) {
   const int dp = d + 1, win = 2 * d + 1, gs = (dp & 1) ? dp : dp + 1;
   const int nbuf = nwin == 1 ? 1 : 2;
   size_t b = (size_t)kpad * dp * 8 + (size_t)(k * dp + (k * dp & 1)) * 8 + (size_t)(kpad / 4) * gs * 16 +
+             (nbuf == 2 ? (size_t)k * 16 : 0) +
              (size_t)kWarps * nbuf * d * kWarpTile * 4 + (size_t)kWarps * kWarpQueue * 4 +
              (size_t)kWarps * nwin * (k + 1) * win * 4 + 16;
   return (b + 15) & ~size_t(15);

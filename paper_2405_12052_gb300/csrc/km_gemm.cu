@@ -639,23 +639,36 @@ __global__ void __launch_bounds__(256) gemm_tie_kernel(GemmArgs a) {
     }
     float best = 3.0e38f, second = 3.0e38f;
     int kbest = 0;
-    for (int q = 0; q < nc; ++q) {
-      const int c = cand(q);
-      if (c >= a.k) continue;  // padding column (same on the 4 threads)
-      const float* crow = a.ctil + (size_t)c * kGemmD + sub * 16;
+    auto partial = [&](const float4* cr) {  // this thread's 16 coordinates of sum (x~ - c~)^2
       float part = 0.f;
 #pragma unroll
-      for (int j = 0; j < 16; j += 4) {
-        const float4 cv = *reinterpret_cast<const float4*>(crow + j);
-        float u = __fsub_rn(xt[j], cv.x); part = __fmaf_rn(u, u, part);
-        u = __fsub_rn(xt[j + 1], cv.y); part = __fmaf_rn(u, u, part);
-        u = __fsub_rn(xt[j + 2], cv.z); part = __fmaf_rn(u, u, part);
-        u = __fsub_rn(xt[j + 3], cv.w); part = __fmaf_rn(u, u, part);
+      for (int j = 0; j < 4; ++j) {
+        const float4 cv = cr[j];
+        float u = __fsub_rn(xt[4 * j], cv.x); part = __fmaf_rn(u, u, part);
+        u = __fsub_rn(xt[4 * j + 1], cv.y); part = __fmaf_rn(u, u, part);
+        u = __fsub_rn(xt[4 * j + 2], cv.z); part = __fmaf_rn(u, u, part);
+        u = __fsub_rn(xt[4 * j + 3], cv.w); part = __fmaf_rn(u, u, part);
       }
-      part = __fadd_rn(part, __shfl_xor_sync(gmask, part, 1));
-      part = __fadd_rn(part, __shfl_xor_sync(gmask, part, 2));  // identical on the 4 threads
+      return part;
+    };
+    auto take = [&](int c, float part) {
       if (part < best || (part == best && c < kbest)) { second = best; best = part; kbest = c; }
       else if (part < second) second = part;
+    };
+    // two candidates per round (their loads in flight together), taken in
+    // list order; padding columns (c >= K, the same on the 4 threads) skipped
+    for (int q = 0; q < nc; q += 2) {
+      const int c0 = cand(q), c1 = q + 1 < nc ? cand(q + 1) : a.k;
+      const bool v0 = c0 < a.k, v1 = c1 < a.k;
+      float p0 = 0.f, p1 = 0.f;
+      if (v0) p0 = partial(reinterpret_cast<const float4*>(a.ctil + (size_t)c0 * kGemmD + sub * 16));
+      if (v1) p1 = partial(reinterpret_cast<const float4*>(a.ctil + (size_t)c1 * kGemmD + sub * 16));
+      p0 = __fadd_rn(p0, __shfl_xor_sync(gmask, p0, 1));
+      p1 = __fadd_rn(p1, __shfl_xor_sync(gmask, p1, 1));
+      p0 = __fadd_rn(p0, __shfl_xor_sync(gmask, p0, 2));  // identical on the 4 threads
+      p1 = __fadd_rn(p1, __shfl_xor_sync(gmask, p1, 2));
+      if (v0) take(c0, p0);
+      if (v1) take(c1, p1);
     }
     int lab = kbest;
     const float A = a.xa[ii];
