@@ -764,21 +764,48 @@ __global__ void __launch_bounds__(256) gemm_rescue_kernel(GemmArgs a) {
 }
 
 // Points -> 16-bit shifted rows in the swizzled tile layout (BF16, or FP16
-// of 2^ex fl(x - s): an exact power-of-two scaling), ||x~||^2 (rounded up)
-// and an N x d FP32 copy.
-__global__ void gemm_prep_points_kernel(const float* __restrict__ x, int64_t ld, int64_t n, const float* shift,
-                                        unsigned short* xb, float* xa, float* xaos, int f16, float xscale) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+// of 2^ex fl(x - s): an exact power-of-two scaling), ||x~||^2 (rounded up,
+// coordinates in order) and an N x d FP32 copy.  One block of 128 threads
+// per 128-point tile: the d x 128 block of points is staged in shared memory
+// (coalesced reads of the d rows), then the AoS rows and the tile's 16 KB of
+// swizzled 16-byte chunks are written coalesced.  Rows past N are left as
+// they are (the caller zeroes the tile storage).
+constexpr int kPrepPad = kGM + 1;
+__global__ void __launch_bounds__(kGM) gemm_prep_points_kernel(const float* __restrict__ x, int64_t ld, int64_t n,
+                                                             const float* __restrict__ shift, unsigned short* xb,
+                                                             float* xa, float* xaos, int f16, float xscale) {
+  __shared__ float s_x[kGemmD * kPrepPad];  // [j][row]
+  const int tid = threadIdx.x;
+  const int64_t base = (int64_t)blockIdx.x * kGM;
+  const int rows = (int)min((int64_t)kGM, n - base);
+  for (int j = 0; j < kGemmD; ++j) s_x[j * kPrepPad + tid] = tid < rows ? x[(int64_t)j * ld + base + tid] : 0.f;
+  __syncthreads();
+  if (tid < rows) {
     float A = 0.f;
     for (int j = 0; j < kGemmD; ++j) {
-      const float v = x[(int64_t)j * ld + i];
-      const float t = __fsub_rn(v, shift[j]);
-      xaos[i * kGemmD + j] = v;
-      xb[swz_index(i, j)] = f16 ? __half_as_ushort(__float2half_rn(t * xscale))
-                                : __bfloat16_as_ushort(__float2bfloat16_rn(t));
+      const float t = __fsub_rn(s_x[j * kPrepPad + tid], shift[j]);
       A = __fmaf_ru(t, t, A);
     }
-    xa[i] = A;
+    xa[base + tid] = A;
+  }
+  for (int q = tid; q < rows * kGemmD; q += kGM) {
+    const int r = q / kGemmD, j = q - r * kGemmD;
+    xaos[(base + r) * kGemmD + j] = s_x[j * kPrepPad + r];
+  }
+  // 16-byte chunk p of row r holds coordinates 8 (p ^ (r & 7)) .. + 7
+  for (int e = tid; e < rows * 8; e += kGM) {
+    const int r = e >> 3, p = e & 7, c = p ^ (r & 7);
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int j0 = 8 * c + 2 * h;
+      const float t0 = __fsub_rn(s_x[j0 * kPrepPad + r], shift[j0]);
+      const float t1 = __fsub_rn(s_x[(j0 + 1) * kPrepPad + r], shift[j0 + 1]);
+      const uint32_t u0 = f16 ? __half_as_ushort(__float2half_rn(t0 * xscale)) : __bfloat16_as_ushort(__float2bfloat16_rn(t0));
+      const uint32_t u1 = f16 ? __half_as_ushort(__float2half_rn(t1 * xscale)) : __bfloat16_as_ushort(__float2bfloat16_rn(t1));
+      w[h] = u0 | (u1 << 16);
+    }
+    *reinterpret_cast<uint4*>(xb + (base + r) * kGemmD + p * 8) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -931,9 +958,9 @@ cudaError_t launch_gemm_prep_points(const float* x, int64_t ld, int64_t n, const
   // rows past N (to the next tile boundary) stay zero
   cudaError_t e = cudaMemsetAsync(xb, 0, (size_t)gemm_xb_rows(n) * kGemmD * 2, st);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
-  gemm_prep_points_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, ld, n, shift, reinterpret_cast<unsigned short*>(xb),
-                                                            xa, xaos, f16, std::ldexp(1.f, ex));
+  const int64_t blocks = (n + kGM - 1) / kGM;  // < 2^24 (N < 2^31)
+  gemm_prep_points_kernel<<<(unsigned)blocks, kGM, 0, st>>>(x, ld, n, shift, reinterpret_cast<unsigned short*>(xb),
+                                                           xa, xaos, f16, std::ldexp(1.f, ex));
   return cudaGetLastError();
 }
 

@@ -278,14 +278,23 @@ __global__ void scan_range_kernel(const float* __restrict__ x, int64_t ld, int64
   const float* row = x + (int64_t)j * ld;
   uint32_t lo = 0xffffffffu, hi = 0u;
   unsigned long long bad = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float v = row[i];
-    if (!isfinite(v)) { ++bad; continue; }
+  auto take = [&](float v) {
+    if (!isfinite(v)) { ++bad; return; }
     const uint32_t o = ordered(v);
     lo = min(lo, o);
     hi = max(hi, o);
+  };
+  // four loads in flight per thread (min and max do not depend on the order)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    const float v0 = row[i], v1 = row[i + stride], v2 = row[i + 2 * stride], v3 = row[i + 3 * stride];
+    take(v0);
+    take(v1);
+    take(v2);
+    take(v3);
   }
+  for (; i < n; i += stride) take(row[i]);
   for (int off = 16; off > 0; off >>= 1) {
     lo = min(lo, __shfl_down_sync(0xffffffffu, lo, off));
     hi = max(hi, __shfl_down_sync(0xffffffffu, hi, off));
@@ -303,8 +312,23 @@ __global__ void scan_range_kernel(const float* __restrict__ x, int64_t ld, int64
 __global__ void scan_amax_kernel(const float* __restrict__ x, int64_t ld, int64_t n, int d,
                                  const float* __restrict__ shift, unsigned int* amax_bits) {
   uint32_t best = 0u;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  // two points per thread and round, their coordinate loads issued together
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + stride < n; i += 2 * stride) {
+    const int64_t i1 = i + stride;
+    float t = __fsub_rn(x[i], shift[0]), u = __fsub_rn(x[i1], shift[0]);
+    float A = __fmul_rn(t, t), B = __fmul_rn(u, u);
+#pragma unroll 4
+    for (int j = 1; j < d; ++j) {
+      t = __fsub_rn(x[(int64_t)j * ld + i], shift[j]);
+      u = __fsub_rn(x[(int64_t)j * ld + i1], shift[j]);
+      A = __fmaf_rn(t, t, A);
+      B = __fmaf_rn(u, u, B);
+    }
+    best = max(best, max(__float_as_uint(A), __float_as_uint(B)));
+  }
+  for (; i < n; i += stride) {
     float t = __fsub_rn(x[i], shift[0]);
     float A = __fmul_rn(t, t);
     for (int j = 1; j < d; ++j) {
