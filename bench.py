@@ -456,6 +456,33 @@ def run_batch(args, ws, rank, local):
     evals = float(np.sum(ns * ks * iters))
     mu_batch = b.split_centroids(r["centroids"])
     b.close()
+    # end to end through the public API: points from pinned host memory in,
+    # labels and centroids out (launch shape from the tuner above)
+    flat_p = torch.from_numpy(flat).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    b2 = km.KMeansBatch(ns, ds, ks)
+    b2.set_points(flat_p)
+    b2.set_init(mus)
+    b2.set_shape(tile, thr)
+    r2 = b2.run(300, 1e-6, want_labels=True)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    b2.close()
+    # roofline of the assign kernel with every instance active: sum_i 3 N_i K_i d_i
+    # flops per launch over the tuner's time of the chosen launch shape
+    pk, src = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    assign_ms = min(info["tune_ms"]) if info["tune_ms"] else None
+    flops = float(np.sum(3.0 * ns * ks * ds))
+    roof = None
+    if assign_ms:
+        ach = flops / (assign_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                "traffic": None, "kernel": "batch_assign_kernel", "kernel_ms": assign_ms,
+                "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x sm_max_mhz ({src} peaks); "
+                               "algorithmic sum_i 3 N_i K_i d_i flops per launch with every instance active"}
     # plain km_run, one instance after another
     sel = list(range(0, len(insts), max(1, args.plain_every)))
     plain_s = 0.0
@@ -481,7 +508,11 @@ def run_batch(args, ws, rank, local):
                       "n_range": [int(ns.min()), int(ns.max())], "d": [2, 3], "k_range": [int(ks.min()), int(ks.max())],
                       "init": "seeded distinct points per instance", "tol": 1e-6, "max_iter": 300,
                       "l2": "points %.1f GB > 129 MB L2" % (flat.nbytes / 1e9), "parallelism": "single"},
-           "clocks": clk, "e2e": None, "gpu_launches": None,
+           "clocks": clk,
+           "e2e": {"value": evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(flat.nbytes + mus.nbytes),
+                   "d2h_bytes_per_step": int(ns.sum() * 4 + mus.nbytes), "time_to_converge_s": e2e_s,
+                   "note": "one 'step' here is the whole batch run to convergence"},
+           "gpu_launches": int(2 * 4 * ((int(iters.max()) + 3) // 4)), "roofline": roof,
            "time_to_converge_s": batch_s, "plain_sequential_s": plain_s * scale,
            "plain_timed_instances": len(sel), "speedup_vs_plain": plain_s * scale / batch_s,
            "same_results_as_plain": bool(same), "iters_total": int(iters.sum()), "iters_max": int(iters.max()),

@@ -98,7 +98,8 @@ __device__ __forceinline__ void btop2(float& b, float& s, int& i, float v, int c
 // the oracle's order.  Then labels and the fixed-point limb sums.
 template <int D>
 __device__ __forceinline__ void tile_points(const BatchArgs& a, const BatchInst& bi,
-                                            const unsigned long long* __restrict__ w2, int* s_acc, int start,
+                                            const unsigned long long* __restrict__ w2,
+                                            const float* __restrict__ rc, int* s_acc, int start,
                                             int count, float B_max, int& myflag, int& my64) {
   const int k = bi.k;
   constexpr int W = 2 * D + 1;
@@ -108,6 +109,7 @@ __device__ __forceinline__ void tile_points(const BatchArgs& a, const BatchInst&
     const bool two = p + step < count;
     float xo[2][D], A[2] = {0.f, 0.f};
     unsigned long long X[D];
+    float tt[2][D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       const float* row = a.x + bi.x_off + (int64_t)j * bi.n + start;
@@ -117,19 +119,56 @@ __device__ __forceinline__ void tile_points(const BatchArgs& a, const BatchInst&
       A[0] = __fmaf_rn(t0, t0, A[0]);
       A[1] = __fmaf_rn(t1, t1, A[1]);
       X[j] = bpack(t0, t1);
+      tt[0][j] = t0;
+      tt[1][j] = t1;
     }
-    float b[2] = {3.0e38f, 3.0e38f}, sv[2] = {3.0e38f, 3.0e38f};
-    int ib[2] = {0, 0};
-    for (int c = 0; c < k; ++c) {
-      const ulonglong2 wa = *reinterpret_cast<const ulonglong2*>(w2 + 4 * c);
-      const ulonglong2 wb = *reinterpret_cast<const ulonglong2*>(w2 + 4 * c + 2);
-      unsigned long long r = bfma2(X[0], wa.x, wb.y);
-      if constexpr (D > 1) r = bfma2(X[1], wa.y, r);
-      if constexpr (D > 2) r = bfma2(X[2], wb.x, r);
-      float v0, v1;
-      bunpack(r, v0, v1);
-      btop2(b[0], sv[0], ib[0], v0, c);
-      btop2(b[1], sv[1], ib[1], v1, c);
+    // Groups of four centroids (the table is padded to a multiple of four
+    // with values of 3e38): only each group's minimum enters the running
+    // best / runner-up (with the group's first index)...
+    float gb[2] = {3.0e38f, 3.0e38f}, gs[2] = {3.0e38f, 3.0e38f};
+    int gi[2] = {0, 0};
+    const int k4 = (k + 3) & ~3;
+    for (int c = 0; c < k4; c += 4) {
+      float v[4][2];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const ulonglong2 wa = *reinterpret_cast<const ulonglong2*>(w2 + 4 * (c + q));
+        const ulonglong2 wb = *reinterpret_cast<const ulonglong2*>(w2 + 4 * (c + q) + 2);
+        unsigned long long r = bfma2(X[0], wa.x, wb.y);
+        if constexpr (D > 1) r = bfma2(X[1], wa.y, r);
+        if constexpr (D > 2) r = bfma2(X[2], wb.x, r);
+        bunpack(r, v[q][0], v[q][1]);
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        float m;
+        asm("min.f32 %0, %1, %2, %3;" : "=f"(m) : "f"(v[0][e]), "f"(v[1][e]), "f"(v[2][e]));
+        btop2(gb[e], gs[e], gi[e], fminf(m, v[3][e]), c);
+      }
+    }
+    // ...then the winning group is evaluated again with the same FMA chain
+    // for the argmin (first index on equal values) and the group's own
+    // runner-up: b = the minimum, sv = the second smallest value over all K.
+    float b[2], sv[2];
+    int ib[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      float best = 3.0e38f, sec = gs[e];
+      int kb = gi[e];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = gi[e] + q;
+        // the same coefficients, by coefficient (rc[j][c]): threads of a warp
+        // read different centroids here, and this layout spreads them over banks
+        float r = __fmaf_rn(tt[e][0], rc[c], rc[3 * kBatchMaxK + c]);
+        if constexpr (D > 1) r = __fmaf_rn(tt[e][1], rc[kBatchMaxK + c], r);
+        if constexpr (D > 2) r = __fmaf_rn(tt[e][2], rc[2 * kBatchMaxK + c], r);
+        if (r < best) { sec = fminf(sec, best); best = r; kb = c; }
+        else sec = fminf(sec, r);
+      }
+      b[e] = best;
+      sv[e] = sec;
+      ib[e] = kb;
     }
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -172,6 +211,7 @@ __device__ __forceinline__ void tile_points(const BatchArgs& a, const BatchInst&
 
 __global__ void __launch_bounds__(kBatchMaxThreads) batch_assign_kernel(BatchArgs a) {
   __shared__ __align__(16) unsigned long long s_w2[kBatchMaxK * 4];  // duplicated screen table
+  __shared__ float s_rc[4 * kBatchMaxK];  // the same coefficients by coefficient: [j][c], n' at j = 3
   __shared__ int s_acc[kBatchMaxK * 7];      // per cluster: count, hi limbs, lo limbs
   __shared__ int s_nflag, s_n64;
   const int tid = threadIdx.x;
@@ -182,24 +222,31 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_assign_kernel(BatchArg
     if (a.state[inst].done) continue;  // block-uniform
     const BatchInst bi = a.inst[inst];
     const int d = bi.d, k = bi.k, w = 2 * d + 1;
-    for (int c = tid; c < k; c += blockDim.x) {
-      float n = 0.f, m[3] = {0.f, 0.f, 0.f};
-      for (int j = 0; j < d; ++j) {
-        const float cv = a.ctil[bi.mu_off + c * d + j];
-        n = __fmaf_rn(cv, cv, n);
-        m[j] = -2.f * cv;  // exact
+    for (int c = tid; c < ((k + 3) & ~3); c += blockDim.x) {
+      float n = 3.0e38f, m[3] = {0.f, 0.f, 0.f};  // padding centroids: value 3e38 for every point
+      if (c < k) {
+        n = 0.f;
+        for (int j = 0; j < d; ++j) {
+          const float cv = a.ctil[bi.mu_off + c * d + j];
+          n = __fmaf_rn(cv, cv, n);
+          m[j] = -2.f * cv;  // exact
+        }
       }
       s_w2[4 * c + 0] = bpack(m[0], m[0]);
       s_w2[4 * c + 1] = bpack(m[1], m[1]);
       s_w2[4 * c + 2] = bpack(m[2], m[2]);
       s_w2[4 * c + 3] = bpack(n, n);
+      s_rc[c] = m[0];
+      s_rc[kBatchMaxK + c] = m[1];
+      s_rc[2 * kBatchMaxK + c] = m[2];
+      s_rc[3 * kBatchMaxK + c] = n;
     }
     for (int q = tid; q < k * w; q += blockDim.x) s_acc[q] = 0;
     __syncthreads();
     const float B_max = a.state[inst].B_max;
-    if (d == 3) tile_points<3>(a, bi, s_w2, s_acc, tl.y, tl.z, B_max, myflag, my64);
-    else if (d == 2) tile_points<2>(a, bi, s_w2, s_acc, tl.y, tl.z, B_max, myflag, my64);
-    else tile_points<1>(a, bi, s_w2, s_acc, tl.y, tl.z, B_max, myflag, my64);
+    if (d == 3) tile_points<3>(a, bi, s_w2, s_rc, s_acc, tl.y, tl.z, B_max, myflag, my64);
+    else if (d == 2) tile_points<2>(a, bi, s_w2, s_rc, s_acc, tl.y, tl.z, B_max, myflag, my64);
+    else tile_points<1>(a, bi, s_w2, s_rc, s_acc, tl.y, tl.z, B_max, myflag, my64);
     __syncthreads();
     long long* prow = a.partials + a.tile_poff[t];
     for (int q = tid; q < k * (d + 1); q += blockDim.x) {
