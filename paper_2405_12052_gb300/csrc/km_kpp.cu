@@ -4,7 +4,7 @@
 // centres).  The K uniforms are inputs, so a run is reproducible and the
 // oracle can take the same ones.
 //
-// Round 0 picks floor(u_0 N).  Round c >= 1: D^2_i = min over chosen centres
+// Pick 0 is floor(u_0 N).  Pick c >= 1: D^2_i = min over chosen centres
 // of sum_j (x_ij - m_j)^2 in FP64 (coordinates in order, no fused
 // multiply-add: the oracle's expression), total = sum_i D^2_i, target =
 // u_c * total, and the pick is the first i whose running sum exceeds the

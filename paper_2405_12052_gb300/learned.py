@@ -7,7 +7,7 @@ Gaussian mixtures (d = 3, K = 16 components: Haar rotations, axis standard
 deviations uniform in [0.5, 2], means uniform in [-50, 50]^3, Dirichlet(1)
 weights) with, as targets, the centres the plain method converges to from
 the generating means (``KMeansBatch``, tol 1e-6).  The k-means++ start plus
-Lloyd remains the fallback and the judge of the final objective
+Lloyd remains the fallback and decides by the final objective
 (``run_with_fallback``).
 
 Only array plumbing (drawing the synthetic mixtures, gathering batches) uses
@@ -189,9 +189,9 @@ def init_multi(g: KMeans, net: SetNet, x, *, hypotheses: int = 64, sample_n: int
 
 
 def run_with_fallback(g: KMeans, net: SetNet, uniforms, *, sample_n: int = 4096, seed: int = 0,
-                      max_iter: int = 300, tol: float = 1e-6, judge: bool = True, hypotheses: int = 1,
+                      max_iter: int = 300, tol: float = 1e-6, fallback: bool = True, hypotheses: int = 1,
                       x=None) -> dict:
-    """Learned start + Lloyd; with ``judge``, also k-means++ (the given K
+    """Learned start + Lloyd; with ``fallback``, also k-means++ (the given K
     uniforms) + Lloyd, keeping the learned result only if its objective is
     within 1e-6 relative of the k-means++ result's (else the fallback).
     hypotheses > 1 takes the rotated-sample start (init_multi; x = the
@@ -206,7 +206,7 @@ def run_with_fallback(g: KMeans, net: SetNet, uniforms, *, sample_n: int = 4096,
     t_learned = time.perf_counter() - t0
     out = dict(iters_learned=r["iters"], objective_learned=obj, wall_learned=t_learned,
                centroids=r["centroids"], used="learned")
-    if judge:
+    if fallback:
         t1 = time.perf_counter()
         g.init_kmeanspp(uniforms)
         rp = g.run(max_iter, tol, want_labels=False)

@@ -3,7 +3,7 @@
 * Training on the GPU kernels lowers the held-out Chamfer loss.
 * The committed network (trained on 200,000 mixtures) has a lower held-out
   loss than the untrained one.
-* Learned start + Lloyd with the k-means++ judge never ends with an
+* Learned start + Lloyd with the k-means++ fallback never ends with an
   objective above the k-means++ result's (beyond 1e-6 relative); the
   iterations and objectives of both starts are printed."""
 import json
@@ -68,7 +68,7 @@ def test_committed_network_and_fallback(km, oracle):
 def test_rotated_sample_start(km, oracle):
     """init_multi: the start is the converged sample centres of the
     hypothesis with the lowest sample objective (checked against the oracle
-    on the sample), and the judged run never ends above the k-means++
+    on the sample), and the run checked against k-means++ never ends above its
     objective by more than 1e-6 relative."""
     import torch
     from paper_2405_12052_gb300 import learned
