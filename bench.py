@@ -581,6 +581,57 @@ def run_learned(args, ws, rank, local):
     return 0
 
 
+def run_kmeanspp(args, ws, rank, local):
+    """GPU k-means++ seeding (K rounds of D^2 sampling) on the points of the
+    1e8-point workload: N*K point-centre distances per seeding, in FP64."""
+    import numpy as np
+    w = load_workload("plain_3d_n1e8_k32", args.n)
+    x, k = w["x"], w["k"]
+    d, n = x.shape
+    import torch
+    import paper_2405_12052_gb300 as km
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    km.build()
+    g = km.KMeans(n, d, k)
+    g.set_points(torch.from_numpy(x).to(dev), borrow=True)
+    us = [np.random.default_rng(100 + r).random(k) for r in range(args.warmup + args.steps)]
+    for r in range(args.warmup):
+        g.init_kmeanspp(us[r])
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    times = []
+    for r in range(args.steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g.init_kmeanspp(us[args.warmup + r])
+        torch.cuda.synchronize(dev)
+        times.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+    g.close()
+    t = statistics.median(times)
+    flops = 3.0 * d * n * k  # per point and round: d FP64 subtractions, squares and adds
+    ach = flops / t / 1e12
+    out = {"metric": METRIC, "value": n * k / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"kmeanspp_3d_n{n}_k{k}", "n": n, "d": d, "k": k,
+                      "step": "one k-means++ seeding (K rounds), host wall time around the call",
+                      "parallelism": "single"},
+           "clocks": clk, "e2e": None, "gpu_launches": 2 * k - 1,
+           "roofline": {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                        "traffic": None, "kernel": "kpp_d2_kernel + kpp_pick_kernel",
+                        "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak); 3 N K d FP64 flops "
+                                       "per seeding",
+                        "hbm_frac_of_measured": (n * (4 * d + 16) * k / t / 1e9) / float(peaks()[0].get("hbm_gbs", 6800.0))}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # The paper's OpenACC times to converge (seconds; its own data, random start
 # and unnamed GPU: context only), tables 4 and 5.
 PAPER_OPENACC_S = {("2d", 100_000, 8): 0.7213, ("2d", 200_000, 8): 0.283524, ("2d", 500_000, 8): 0.518219,
@@ -667,6 +718,8 @@ def main():
         return run_learned(args, ws, rank, local)
     if args.workload == "paper_sweep":
         return run_sweep(args, ws, rank, local)
+    if args.workload == "kmeanspp":
+        return run_kmeanspp(args, ws, rank, local)
     return run_ours(args, ws, rank, local)
 
 
