@@ -105,16 +105,30 @@ __device__ __forceinline__ void tile_points(const BatchArgs& a, const BatchInst&
   constexpr int W = 2 * D + 1;
   const float sB = sqrtf(B_max);
   const int step = blockDim.x;
+  // the next round's two points are loaded while this round's are screened
+  auto load = [&](int pp, float (&dst)[2][D]) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const float* row = a.x + bi.x_off + (int64_t)j * bi.n + start;
+      dst[0][j] = row[pp];
+      dst[1][j] = pp + step < count ? row[pp + step] : dst[0][j];
+    }
+  };
+  float nxt[2][D];
+  if (threadIdx.x < count) load(threadIdx.x, nxt);
   for (int p = threadIdx.x; p < count; p += 2 * step) {
     const bool two = p + step < count;
     float xo[2][D], A[2] = {0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      xo[0][j] = nxt[0][j];
+      xo[1][j] = nxt[1][j];
+    }
+    if (p + 2 * step < count) load(p + 2 * step, nxt);
     unsigned long long X[D];
     float tt[2][D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      const float* row = a.x + bi.x_off + (int64_t)j * bi.n + start;
-      xo[0][j] = row[p];
-      xo[1][j] = two ? row[p + step] : xo[0][j];
       const float t0 = __fsub_rn(xo[0][j], bi.s[j]), t1 = __fsub_rn(xo[1][j], bi.s[j]);
       A[0] = __fmaf_rn(t0, t0, A[0]);
       A[1] = __fmaf_rn(t1, t1, A[1]);
