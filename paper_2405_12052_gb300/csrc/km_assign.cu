@@ -40,22 +40,6 @@ __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
   asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
 }
-__device__ __forceinline__ float4 ld_stream4(const float* p) {
-  float4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-  return v;
-}
-
-// Top-2 of packed (value, index) floats, two new candidates at a time:
-// m1' = min(m1, a, b); m2' = min(m2, max(a, b), max(m1, min(a, b))).
-__device__ __forceinline__ void top2_pair(float& m1, float& m2, float a, float b) {
-  float lo = fminf(a, b), hi = fmaxf(a, b);
-  float t = fmaxf(m1, lo);
-  m2 = fmin3(m2, hi, t);
-  m1 = fminf(m1, lo);
-}
-
 // Exact split of x into the two fixed-point limbs (biased bit patterns).
 __device__ __forceinline__ void split_limbs(float x, float C_hi, float C_lo, uint32_t& bhi,
                                             uint32_t& blo) {

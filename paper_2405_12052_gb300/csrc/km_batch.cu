@@ -32,12 +32,6 @@ namespace {
 constexpr float kBU = 5.9604644775390625e-08f;            // 2^-24
 constexpr float kBU64x = 1.1102230246251565e-16f * 4.1f;  // 4.1 * 2^-53
 
-// |FP32 direct form - FP64 oracle distance| (d <= 3), as for the single path.
-__device__ __forceinline__ float bbound(float dv, float sA, float sB, float AB, int d) {
-  const float sd = sqrtf(fmaxf(dv, 0.f));
-  return 1.01f * kBU * ((float)(d + 2) * dv + 2.f * sd * (sA + sB)) + kBU64x * (float)(d + 1) * AB + 1e-30f;
-}
-
 __device__ __forceinline__ double bd64(const float* xo, const double* mu_k, int d) {
   double acc = 0.0;
   for (int j = 0; j < d; ++j) {

@@ -507,7 +507,6 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
       // (or a point whose halves did not fit) to the rescue list; both are
       // decided exactly by separate kernels.
       {
-        const unsigned gmask = 0xFu << (lane & ~3);
         const int64_t ii = tile * kGM + pp;
         const int nc = es.cnt[pp];
         const bool over = es.over[pp] != 0;

@@ -59,7 +59,6 @@ __device__ void prepare_tables(const UpdateArgs& a, double* sB) {
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nth = blockDim.x * blockDim.y;
   const int k = a.k, d = a.d;
-  __shared__ double sh_bmax;
   __shared__ int sh_sigma;
   __shared__ double sh_M, sh_dummy;
   if (a.fast) {
@@ -114,7 +113,6 @@ __device__ void prepare_tables(const UpdateArgs& a, double* sB) {
       ic.B_max = __double2float_ru(bmax);
       ic.pad[0] = ic.pad[1] = ic.pad[2] = 0.f;
       *a.ic = ic;
-      sh_bmax = bmax;
       sh_sigma = sigma;
       sh_M = M;
       sh_dummy = (L <= 6 ? ldexp(2.0 - 0x1p-23, eM) : ldexp(1.5 - 0x1p-23, eM));
