@@ -218,18 +218,26 @@ __device__ __forceinline__ void tile_points(const BatchArgs& a, const BatchInst&
 }
 
 __global__ void __launch_bounds__(kBatchMaxThreads) batch_assign_kernel(BatchArgs a) {
-  __shared__ __align__(16) unsigned long long s_w2[kBatchMaxK * 4];  // duplicated screen table
-  __shared__ float s_rc[4 * kBatchMaxK];  // the same coefficients by coefficient: [j][c], n' at j = 3
-  __shared__ int s_acc[kBatchMaxK * 7];      // per cluster: count, hi limbs, lo limbs
+  // two sets of the per-tile shared arrays, alternating between the tiles a
+  // block takes: a tile's table and sums are rebuilt only two tiles later,
+  // after two block barriers, so no barrier is needed between tiles
+  __shared__ __align__(16) unsigned long long s_w2b[2][kBatchMaxK * 4];  // duplicated screen table
+  __shared__ float s_rcb[2][4 * kBatchMaxK];  // the same coefficients by coefficient: [j][c], n' at j = 3
+  __shared__ int s_accb[2][kBatchMaxK * 7];   // per cluster: count, hi limbs, lo limbs
   __shared__ int s_nflag, s_n64;
   const int tid = threadIdx.x;
   int my64 = 0, myflag = 0;
+  int par = 0;  // tiles this block has processed, mod 2 (block-uniform)
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     const int4 tl = a.tiles[t];
     const int inst = tl.x;
     if (a.state[inst].done) continue;  // block-uniform
     const BatchInst bi = a.inst[inst];
     const int d = bi.d, k = bi.k, w = 2 * d + 1;
+    unsigned long long* s_w2 = s_w2b[par];
+    float* s_rc = s_rcb[par];
+    int* s_acc = s_accb[par];
+    par ^= 1;
     for (int c = tid; c < ((k + 3) & ~3); c += blockDim.x) {
       float n = 3.0e38f, m[3] = {0.f, 0.f, 0.f};  // padding centroids: value 3e38 for every point
       if (c < k) {
@@ -262,7 +270,6 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_assign_kernel(BatchArg
       const int* acc = s_acc + c * w;
       prow[q] = j == d ? (long long)acc[0] : ((long long)acc[1 + j] << 22) + (long long)acc[1 + d + j];
     }
-    __syncthreads();  // the tables and sums are reused by the next tile
   }
   if (tid == 0) { s_nflag = 0; s_n64 = 0; }
   __syncthreads();
