@@ -20,7 +20,8 @@
  *     point i is at x[j * ld + i] (KM_SOA_DxN), or row-major N x d
  *     (KM_AOS_NxD, copied into the SoA layout on entry).
  *   - Centroids are double, K x d, row-major.  Labels are int32 in 0..K-1
- *     (the paper numbers clusters 1..K).
+ *     (the paper numbers clusters 1..K); a context may keep them as bytes
+ *     (km_options.label_bytes = 1, K <= 256).
  *   - Labels are exact: every point's label equals the argmin of the
  *     double-precision squared distances sum_j (x_ij - mu_kj)^2 accumulated
  *     over j in order, ties to the lowest k.  Points whose two nearest FP32
