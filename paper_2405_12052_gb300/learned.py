@@ -99,9 +99,22 @@ def init_params(d: int, k: int, seed: int = 0, h: int = 128) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
+def _rotations(m: int, d: int, g, device):
+    """m seeded Haar-random orthogonal maps (QR of Gaussian matrices, signs
+    fixed: rotations and reflections), as a (m, d, d) float32 tensor."""
+    import torch
+    a = torch.randn(m, d, d, generator=g, device=device, dtype=torch.float64)
+    q, r = torch.linalg.qr(a)
+    q = q * torch.sign(torch.diagonal(r, dim1=-2, dim2=-1)).unsqueeze(-2)
+    return q.to(torch.float32)
+
+
 def train(x, t, *, epochs: int = 3, batch: int = 64, lr: float = 1e-3, lr_min: float = 1e-5, seed: int = 0,
-          log_every: int = 200, val=None, log=print):
-    """Adam on the symmetric Chamfer loss, cosine learning-rate decay."""
+          log_every: int = 200, val=None, log=print, rotate: bool = False):
+    """Adam on the symmetric Chamfer loss, cosine learning-rate decay.  With
+    ``rotate`` every batch's sets and targets are turned by seeded Haar
+    rotations about the origin (data augmentation: the network then meets
+    the rotated samples that init_multi gives it)."""
     import torch
     count, S, d = x.shape
     k = t.shape[1]
@@ -117,6 +130,10 @@ def train(x, t, *, epochs: int = 3, batch: int = 64, lr: float = 1e-3, lr_min: f
         for s0 in range(0, count - batch + 1, batch):
             idx = perm[s0:s0 + batch]
             xb, tb = x[idx].contiguous(), t[idx].contiguous()
+            if rotate:
+                rot = _rotations(batch, d, g, x.device)
+                xb = torch.bmm(xb, rot.transpose(1, 2)).contiguous()
+                tb = torch.bmm(tb, rot.transpose(1, 2)).contiguous()
             rate = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * step / max(1, steps)))
             want = (step % log_every) == 0 or step == steps - 1
             loss = net.train_step(xb, tb, rate, want_loss=want)
@@ -135,8 +152,10 @@ def save(net: SetNet, path: str, meta: dict):
     np.savez(path, params=net.params(), d=net.d, k=net.k, meta=json.dumps(meta))
 
 
-def load(path: str = WEIGHTS) -> SetNet:
-    z = np.load(path)
+def load(path: str | None = None) -> SetNet:
+    """The network from a weights file (default: KM_SETNET_WEIGHTS if set,
+    else the committed weights)."""
+    z = np.load(path or os.environ.get("KM_SETNET_WEIGHTS", WEIGHTS))
     net = SetNet(int(z["d"]), int(z["k"]))
     net.set_params(z["params"])
     return net
@@ -229,6 +248,7 @@ def main(argv=None):
     tr.add_argument("--lr", type=float, default=1e-3)
     tr.add_argument("--seed", type=int, default=0)
     tr.add_argument("--out", default=WEIGHTS)
+    tr.add_argument("--rotate", action="store_true", help="augment with random rotations")
     a = ap.parse_args(argv)
     if a.cmd == "train":
         dev = torch.device("cuda")
@@ -241,8 +261,9 @@ def main(argv=None):
         print(json.dumps({"generate_s": gen_s, "targets_s": tgt_s, "target_iters_mean": float(its.mean())}))
         xv, tv = x[a.mixtures:].contiguous(), tgt[a.mixtures:].contiguous()
         net, hist = train(x[:a.mixtures], tgt[:a.mixtures], epochs=a.epochs, batch=a.batch, lr=a.lr,
-                          seed=a.seed, val=(xv[:256], tv[:256]))
+                          seed=a.seed, val=(xv[:256], tv[:256]), rotate=a.rotate)
         meta = dict(mixtures=a.mixtures, epochs=a.epochs, batch=a.batch, lr=a.lr, seed=a.seed, S=4096,
+                    rotate=a.rotate,
                     generate_s=gen_s, targets_s=tgt_s, final=hist[-1], history=hist[::5])
         save(net, a.out, meta)
         print(json.dumps({"saved": a.out, "final": hist[-1]}))
