@@ -477,9 +477,11 @@ km_status km_set_points(km_ctx* c, const float* x, int64_t ld, int32_t layout, i
     shift[j] = (float)(0.5 * (lo + hi));
     absmax = std::max(absmax, std::max(std::fabs(lo), std::fabs(hi)));
   }
-  int ex = absmax > 0.0 ? (int)std::floor(std::log2(absmax)) + 2 : -60;
+  int ex = absmax > 0.0 ? (int)std::floor(std::log2(absmax)) + 2 : -104;
   if (absmax > 0.0 && std::ldexp(1.0, ex - 1) <= absmax) ++ex;  // guard log2 rounding
-  ex = std::max(ex, -60);
+  // C_lo = 1.5 * 2^(ex - 21) must stay a normal float: ex >= -104 (data
+  // below 2^-106 in magnitude is summed on the 2^-148 grid)
+  ex = std::max(ex, -104);
   if (ex > 100) return fail(c, KM_ENUMERIC, "coordinates too large for the fixed-point sums (|x| >= 2^99)");
   DataConst hdc{};
   for (int j = 0; j < kMaxDFast; ++j) hdc.s[j] = j < d ? shift[j] : 0.f;

@@ -428,9 +428,9 @@ __global__ void __launch_bounds__(256) batch_scan_kernel(const float* __restrict
         bi.s[j] = 0.f;
       }
     }
-    int ex = amax > 0.0 ? ilogb(amax) + 2 : -60;
+    int ex = amax > 0.0 ? ilogb(amax) + 2 : -104;
     if (amax > 0.0 && ldexp(1.0, ex - 1) <= amax) ++ex;
-    ex = max(ex, -60);
+    ex = max(ex, -104);  // C_lo = 1.5 * 2^(ex - 21) stays a normal float
     bi.G0 = ex - 44;
     bi.C_hi = ldexpf(1.5f, ex + 1);
     bi.C_lo = ldexpf(1.5f, ex - 21);

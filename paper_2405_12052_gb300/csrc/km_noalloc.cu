@@ -57,11 +57,11 @@ __global__ void na_absmax_kernel(const float* __restrict__ x, int64_t ld, int64_
 // Fixed-point grid from max |x|: x = hi 2^(G0+22) + lo 2^G0, |hi| <= 2^21.
 __device__ __forceinline__ int na_grid_ex(unsigned int absmax_bits) {
   const float amax = __uint_as_float(absmax_bits);
-  if (!(amax > 0.f)) return -60;
+  if (!(amax > 0.f)) return -104;
   int e;
   frexpf(amax, &e);  // amax = m 2^e, m in [0.5, 1)
   int ex = e + 1;    // |x| < 2^(ex - 1)
-  return max(-60, min(ex, 100));
+  return max(-104, min(ex, 100));  // C_lo = 1.5 * 2^(ex - 21) stays a normal float
 }
 
 __global__ void __launch_bounds__(kNaThreads) na_assign_kernel(

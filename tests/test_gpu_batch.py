@@ -129,3 +129,17 @@ def test_batch_objective_matches_the_oracle(km, oracle):
         ref = oracle.run(w["x"], w["mu0"], 100, 1e-6)
         assert abs(objs[i] - ref["objective"]) <= 1e-12 * max(ref["objective"], 1.0), i
     b.close()
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e20])
+def test_batch_extreme_magnitudes(km, oracle, scale):
+    """Instances with coordinates near FP32's underflow or whose squared
+    distances overflow FP32: every instance still equals the oracle's run."""
+    insts = synth.batch_instances(5, seed=31, n_lo=300, n_hi=2_000)
+    for w in insts:
+        w["x"] = (w["x"].astype(np.float64) * scale).astype(np.float32)
+        w["mu0"] = w["x"][:, :w["k"]].T.astype(np.float64).copy()
+    b = _batch(km, insts)
+    r = b.run(30, 0.0)
+    _check_against_oracle(b, insts, r, oracle, 30, 0.0)
+    b.close()
