@@ -413,3 +413,33 @@ def test_extreme_magnitudes(km, oracle, scale, d, k):
     x = (x.astype(np.float64) * scale).astype(np.float32)
     mu0, _ = synth.init_distinct(x, k, seed=72)
     lockstep(km, oracle, x, mu0, steps=2)
+
+
+def test_large_offset_integer_grid(km, oracle):
+    """Every coordinate offset by 1e7, where FP32 spaces values 1.0 apart:
+    the shifted screen and the fixed-point sums stay exact."""
+    x, _, _ = synth.iso_mixture(30_000, 3, 6, sigma=40.0, box=400.0, seed=81, offset=1e7)
+    mu0, _ = synth.init_distinct(x, 6, seed=82)
+    assert lockstep(km, oracle, x, mu0, steps=2)["path"] == 1
+
+
+def test_d4_k256_fused(km, oracle):
+    x, _, _ = synth.aniso_mixture(60_000, 4, 40, seed=83)
+    mu0, _ = synth.init_distinct(x, 256, seed=84)
+    assert lockstep(km, oracle, x, mu0, steps=2)["path"] == 1
+
+
+@pytest.mark.parametrize("label_bytes", [4, 1])
+def test_k_equals_n(km, oracle, label_bytes):
+    """K = N with the points themselves as centres: every point is its own
+    cluster (z_i = i) and the step is a fixed point (E = 0)."""
+    x, _, _ = synth.iso_mixture(200, 3, 4, seed=85)
+    mu0 = x.T.astype(np.float64).copy()
+    g = km.KMeans(200, 3, 200, label_bytes=label_bytes)
+    g.set_points(x)
+    g.set_init(mu0)
+    e, e2 = g.step()
+    assert np.array_equal(g.labels(), np.arange(200)) and e == 0.0 and e2 == 0.0
+    assert np.array_equal(g.counts(), np.ones(200, dtype=np.int64))
+    assert np.array_equal(g.centroids(), mu0)
+    g.close()
