@@ -30,7 +30,8 @@ TC = ["bf16", "f16"]
 
 
 @pytest.mark.parametrize("tc", TC)
-@pytest.mark.parametrize("n,k", [(20_000, 64), (20_000, 300), (5_003, 1024), (129, 7), (1_000, 1), (4_096, 257)])
+@pytest.mark.parametrize("n,k", [(20_000, 64), (20_000, 300), (5_003, 1024), (129, 7), (1_000, 1), (4_096, 257),
+                                 (100, 10), (1, 1), (2, 2)])
 def test_gemm_lockstep(km, oracle, n, k, tc):
     x, _, _ = synth.iso_mixture(n, 64, 40, sigma=1.0, box=10.0, seed=n + k)
     mu0, _ = synth.init_distinct(x, k, seed=k)
