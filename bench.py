@@ -21,6 +21,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -158,10 +159,18 @@ KERNEL_SOURCES = {
 }
 
 
+def code_only(text: str) -> str:
+    """C/CUDA source without comments and blank lines (the traffic records
+    are keyed by a kernel's code, not by its comments)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def source_hash(files=("km_assign.cu", "km_internal.cuh")):
     h = hashlib.sha256()
     for f in files:
-        h.update(open(os.path.join(ROOT, "paper_2405_12052_gb300", "csrc", f), "rb").read())
+        h.update(code_only(open(os.path.join(ROOT, "paper_2405_12052_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -2,10 +2,11 @@
 // half of the mean calculation of Lloyd's algorithm (paper, section "The
 // Lloyd's algorithm", steps 2 and 3), fused in one pass over the points.
 //
-// assign_fast_kernel<D> (d <= 4, K <= 256) is the hot kernel: SoA float4
-// streaming loads, FP32 screen on FFMA2 with the index packed by IMAD and
-// top-2 by FMNMX, a per-block queue of flagged points re-decided at the end
-// of the block's work, and exact integer sums in per-warp shared windows.
+// assign_fast_kernel<D> (d <= 4, K <= 256) is the hot kernel: SoA point
+// tiles staged by 16-byte cp.async copies, FP32 screen on FFMA2 with the
+// group index packed by IMAD and top-2 by FMNMX, per-warp queues of flagged
+// points re-decided in batches, and exact integer sums in per-warp (or
+// per-half-warp) shared windows flushed into the block's int64 totals.
 // assign_generic_kernel handles any d and K with a direct-form FP32 screen,
 // the same re-check rules and 64-bit atomics into the block's own partial row.
 #include "km_internal.cuh"

@@ -8,7 +8,8 @@
 //  * batch_assign_kernel (persistent: CTAs stride over the tile list): per
 //    tile, the instance's screen table in shared memory; per pair of points
 //    the FP32 expanded-form values ||c~||^2 - 2 x~.c~ to all K centres on
-//    coordinates shifted by the instance's shift (paired FMA chains), the
+//    coordinates shifted by the instance's shift (paired FMA chains, minima
+//    of groups of four centres, the winning group evaluated again), the
 //    argmin and runner-up, and the rigorous bound that sends an unresolved
 //    point to FP64 in the oracle's order (lowest index on ties); then exact
 //    fixed-point sums: each coordinate split into
