@@ -26,6 +26,19 @@ bool inject_alloc_failure() {
   }
   return false;
 }
+// The fused kernel's constant-bank screen table exists once per device (a
+// module-level __constant__ array), so at most one context per device may use
+// it at a time: the context that claims it at km_create keeps it until
+// km_destroy; the others read their tables from shared memory.
+static std::atomic<int> g_const_tab_owner[64];
+static bool claim_const_tab(int dev) {
+  if (dev < 0 || dev >= 64) return false;
+  int expected = 0;
+  return g_const_tab_owner[dev].compare_exchange_strong(expected, 1);
+}
+static void release_const_tab(int dev) {
+  if (dev >= 0 && dev < 64) g_const_tab_owner[dev].store(0);
+}
 }  // namespace km
 
 struct km_ctx {
@@ -64,6 +77,7 @@ struct km_ctx {
   unsigned long long* scan_bad = nullptr;
   size_t fast_smem = 0;
   int nwin = 2;  // fused path: sum windows per warp
+  bool const_tab = false;  // this context holds the device's constant-bank screen table
   int path = 0;  // 1 fused (d <= 4, K <= 256), 2 generic, 3 tensor cores (d = 64, K <= 1024)
   // tensor-core path
   void* xb = nullptr;
@@ -119,6 +133,8 @@ cudaError_t dalloc(T** p, size_t count) {
 }
 
 void free_all(km_ctx* c) {
+  if (c->const_tab) release_const_tab(c->dev);
+  c->const_tab = false;
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
   void* bufs[] = {c->x_own, c->labels, c->labels8, c->mu, c->counts, c->partials, c->s128, c->tab2,
@@ -194,6 +210,7 @@ cudaError_t launch_assign(km_ctx* c, bool labels_pass = false) {
     a.nwin = c->nwin;
     a.store_labels = store;
     a.ignore_done = labels_pass ? 1 : 0;
+    a.const_tab = c->const_tab ? 1 : 0;
     e = launch_assign_fast(c->d, c->G, c->fast_smem, c->st, a);
   } else {
     GenericArgs a{};
@@ -326,7 +343,7 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
     KM_CUDA(c, cudaStreamCreate(&c->st));  // blocking: ordered after legacy-stream work
     c->own_stream = true;
   }
-  c->kpad = (k + 3) / 4 * 4;  // the screen works on groups of 4 centroids
+  c->kpad = (k + 7) / 8 * 8;  // the screen works on pairs of groups of 4 centroids
   c->fast = d <= kMaxDFast && k <= kMaxKFast;
   const bool gemm = d == kGemmD && k <= kGemmMaxK && n < (int64_t(1) << 31) &&
                     gemm_smem_bytes((k + 255) / 256 * 256) <= (size_t)p.sharedMemPerBlockOptin;
@@ -334,12 +351,19 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
     // one 32-bit sum window per half-warp (double-buffered points) when it
     // fits with as many resident blocks per SM as one window per warp
     // (single-buffered points) allows, else the smaller layout
+    if (fast_has_const_table(d, c->kpad)) c->const_tab = claim_const_tab(c->dev);
     const size_t s2 = fast_smem_bytes(d, c->kpad, k, 2), s1 = fast_smem_bytes(d, c->kpad, k, 1);
     const size_t lim = (size_t)p.sharedMemPerBlockOptin;
-    const int b2 = s2 <= lim ? fast_blocks_per_sm(d, s2) : 0, b1 = s1 <= lim ? fast_blocks_per_sm(d, s1) : 0;
+    const bool ct = c->const_tab;
+    const int b2 = s2 <= lim ? fast_blocks_per_sm(d, s2, c->kpad, ct) : 0,
+              b1 = s1 <= lim ? fast_blocks_per_sm(d, s1, c->kpad, ct) : 0;
     c->nwin = (b2 > 0 && b2 >= b1) ? 2 : 1;
     c->fast_smem = c->nwin == 2 ? s2 : s1;
     if (c->fast_smem > lim || (c->nwin == 1 ? b1 : b2) == 0) c->fast = false;
+    if (!c->fast && c->const_tab) {
+      release_const_tab(c->dev);
+      c->const_tab = false;
+    }
   }
   const int64_t ntiles = (n + kWarpTile - 1) / kWarpTile;  // warp-tiles of 256 points
   if (c->opt.dist_path == KM_DIST_TENSOR && !gemm)
@@ -353,7 +377,7 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
   } else if (c->fast) {
     // one resident wave; each warp strides over warp-tiles, and no block
     // takes more than 2^19 points (int64 per-block sums stay in range)
-    const int bpsm = fast_blocks_per_sm(d, c->fast_smem);
+    const int bpsm = fast_blocks_per_sm(d, c->fast_smem, c->kpad, c->const_tab);
     int64_t g = std::min<int64_t>((ntiles + kWarps - 1) / kWarps, (int64_t)c->sms * bpsm);
     const int64_t tiles_per_block_max = kMaxPointsPerBlock / kWarpTile;
     g = std::max<int64_t>(g, (ntiles + tiles_per_block_max - 1) / tiles_per_block_max);

@@ -2,11 +2,17 @@
 // half of the mean calculation of Lloyd's algorithm (paper, section "The
 // Lloyd's algorithm", steps 2 and 3), fused in one pass over the points.
 //
-// assign_fast_kernel<D> (d <= 4, K <= 256) is the hot kernel: SoA point
-// tiles staged by 16-byte cp.async copies, FP32 screen on FFMA2 with the
-// group index packed by IMAD and top-2 by FMNMX, per-warp queues of flagged
-// points re-decided in batches, and exact integer sums in per-warp (or
-// per-half-warp) shared windows flushed into the block's int64 totals.
+// assign_fast_kernel<D, KG, CT> (d <= 4, K <= 256) is the hot kernel: SoA
+// point tiles staged by 16-byte cp.async copies; an FP32 screen on FFMA2
+// chains over groups of 4 centroids, the group minima packed with the group
+// index and a running top-2 updated two groups at a time; the winning group
+// recomputed for the label and the runner-up; a flag test in units of the
+// screen's binade; per-warp queues of flagged points re-decided in batches;
+// exact integer sums in per-warp (or per-half-warp) shared windows flushed
+// into the block's int64 totals.  KG > 0 fixes the number of groups at
+// compile time (shift packing, unrolled screen); CT reads the screen table
+// from the constant bank instead of shared memory (no vector registers and
+// no shared-memory loads for the table; one context per device holds it).
 // assign_generic_kernel handles any d and K with a direct-form FP32 screen,
 // the same re-check rules and 64-bit atomics into the block's own partial row.
 #include "km_internal.cuh"
@@ -14,6 +20,8 @@
 namespace km {
 
 namespace {
+
+constexpr int kGpUnroll = 1;  // the shared-memory-table screen keeps its group-pair loop rolled
 
 __device__ __forceinline__ unsigned long long pack2(float a, float b) {
   unsigned long long p;
@@ -161,13 +169,6 @@ __device__ __forceinline__ unsigned long long fsub2(unsigned long long a, unsign
 }
 __device__ __forceinline__ unsigned long long dup2(float v) { return pack2(v, v); }
 
-// Top-2 update of packed (value, index) floats with one new candidate.
-__device__ __forceinline__ void top2_one(float& m1, float& m2, float v) {
-  const float t = fmaxf(m1, v);
-  m1 = fminf(m1, v);
-  m2 = fminf(m2, t);
-}
-
 // Shared memory of the fused kernel.  The windows, point buffers and queues
 // are private to one warp; the int64 totals are the block's (windows are
 // flushed into them with 64-bit shared atomics).  With one window per warp
@@ -232,6 +233,20 @@ __device__ __forceinline__ void flush_windows(uint32_t* wwarp, long long* acc, i
 // warp buffer; chunks past N are zero-filled and read nothing past N.
 template <int D>
 __device__ __forceinline__ void prefetch_tile(const FastArgs& a, float* xb, int64_t base, int lane) {
+  if (base + kWarpTile <= a.n) {  // a full tile: no bounds logic
+#pragma unroll
+    for (int g = 0; g < kNG; ++g) {
+      const int off = g * kGS + 4 * lane;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const float* src = a.x + (int64_t)j * a.ld + base + off;
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(xb + j * kWarpTile + off);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    return;
+  }
 #pragma unroll
   for (int g = 0; g < kNG; ++g) {
     const int off = g * kGS + 4 * lane;
@@ -280,21 +295,146 @@ __device__ void drain_warp_queue(const FastArgs& a, FastSmem<D>& sm, uint32_t* q
   flush_windows<D>(wwarp, acc, a.k, a.nwin, lane, dc.bits_C_hi, dc.bits_C_lo);
 }
 
-// Per-launch constants of the fused kernel, in registers.
+// Per-launch constants of the fused kernel, in registers.  The flag test is
+// evaluated in units of r: a point is accepted when
+//   r2 - r1 > c0 + A cA + tau (r2 - M),
+// r1 <= r2 its two smallest screen values, A = ||x~||^2.  r2 - r1 and r2 - M
+// are exact (one binade); c0 and cA are the ulp-unit constants of the update
+// kernel times the binade's ulp (a power of two).
 struct FastCtx {
-  uint32_t mul, L, kmask, bitsM_low;
-  float thr_c0, thr_cA2, tau;
+  uint32_t mul, L, kmask, ehi;  // ehi: the top L bits shared by every r's bit pattern
+  float M, c0, cA, tau;
   unsigned long long chi2, clo2;
   int k, kpad;
 };
 
+// bits(v) * 2^L + idx: the screen value with an index in its low L bits.
+// With a compile-time L this is a shift and an add (integer ALU pipe).
+template <int LB>
+__device__ __forceinline__ float pack_idx(float v, const FastCtx& cx, uint32_t idx) {
+  if constexpr (LB > 0) return __uint_as_float((__float_as_uint(v) << LB) + idx);
+  else return __uint_as_float(imad(__float_as_uint(v), cx.mul, idx));
+}
+// The screen value r back from a packed value (one funnel shift).
+template <int LB>
+__device__ __forceinline__ float unpack_val(float w, const FastCtx& cx) {
+  return __uint_as_float(__funnelshift_r(__float_as_uint(w), cx.ehi, LB > 0 ? LB : cx.L));
+}
+
+// Screen of one group of 4 centroids (table rows tr) for this lane's 8
+// points: r = n_k + sum_j x~_j a_kj by one FFMA2 chain per pair of points,
+// the group minimum by FMNMX3 + FMNMX, packed with the group's first index.
+template <int D, int LB>
+__device__ __forceinline__ void screen_group(const unsigned long long* tr, const unsigned long long (&X)[D][kPts / 2],
+                                             uint32_t g4, const FastCtx& cx, float (&gm)[kPts]) {
+  constexpr int DP = D + 1;
+  unsigned long long T[4][DP];
+  if constexpr (D <= 3) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int j = 0; j < DP; ++j) T[c][j] = tr[c * DP + j];
+  }
+#pragma unroll
+  for (int pp = 0; pp < kPts / 2; ++pp) {
+    if constexpr (D > 3) {  // reloaded per pair of points: fewer live registers
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < DP; ++j) T[c][j] = tr[c * DP + j];
+    }
+    float v0[4], v1[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      unsigned long long r = T[c][D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) r = ffma2(X[j][pp], T[c][j], r);
+      unpack2(r, v0[c], v1[c]);
+    }
+    gm[2 * pp] = pack_idx<LB>(fminf(fmin3(v0[0], v0[1], v0[2]), v0[3]), cx, g4);
+    gm[2 * pp + 1] = pack_idx<LB>(fminf(fmin3(v1[0], v1[1], v1[2]), v1[3]), cx, g4);
+  }
+}
+
+// Screen table in the constant bank (one process-wide copy per device,
+// kpad <= 64): the compile-time-unrolled screen reads its coefficients as
+// uniform operands, so they take no vector registers and no shared-memory
+// loads.  Written by a device-to-device copy before each launch that uses it.
+__constant__ union {
+  unsigned long long u[kConstTabWords];  // packed (a, a) pairs, as in the global table
+  float f[2 * kConstTabWords];           // f[2 i] = the coefficient of pair i
+} c_screen_tab;
+
+// Running top-2 over groups, two groups at a time: with lo <= hi the pair's
+// packed minima, m1' = min(m1, lo) and m2' = min(m2, hi, max(m1, lo)).
+template <bool FIRST>
+__device__ __forceinline__ void top2_pair(float (&m1)[kPts], float (&m2)[kPts], const float (&ga)[kPts],
+                                          const float (&gb)[kPts]) {
+#pragma unroll
+  for (int p = 0; p < kPts; ++p) {
+    const float lo = fminf(ga[p], gb[p]), hi = fmaxf(ga[p], gb[p]);
+    if constexpr (FIRST) {
+      m1[p] = lo;
+      m2[p] = hi;
+    } else {
+      m2[p] = fmin3(m2[p], hi, fmaxf(m1[p], lo));
+      m1[p] = fminf(m1[p], lo);
+    }
+  }
+}
+
+// Screen of groups G0/4 and G0/4 + 1 (centroids G0 .. G0 + 7) from the
+// constant-bank table, one pair of points at a time: 8 FFMA2 chains, the two
+// group minima per point, and the running top-2 update.  G0 is a
+// compile-time constant after unrolling, so every table operand has a fixed
+// offset.
+template <int D, int LB, bool FIRST>
+__device__ __forceinline__ void screen_pair_ct(int G0, const unsigned long long (&X)[D][kPts / 2], const FastCtx& cx,
+                                               float (&m1)[kPts], float (&m2)[kPts]) {
+  constexpr int DP = D + 1;
+#pragma unroll
+  for (int pp = 0; pp < kPts / 2; ++pp) {
+    float a0[4], a1[4], b0[4], b1[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      unsigned long long ra = c_screen_tab.u[(G0 + c) * DP + D], rb = c_screen_tab.u[(G0 + 4 + c) * DP + D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        ra = ffma2(X[j][pp], c_screen_tab.u[(G0 + c) * DP + j], ra);
+        rb = ffma2(X[j][pp], c_screen_tab.u[(G0 + 4 + c) * DP + j], rb);
+      }
+      unpack2(ra, a0[c], a1[c]);
+      unpack2(rb, b0[c], b1[c]);
+    }
+    const float ga[2] = {pack_idx<LB>(fminf(fmin3(a0[0], a0[1], a0[2]), a0[3]), cx, (uint32_t)G0),
+                         pack_idx<LB>(fminf(fmin3(a1[0], a1[1], a1[2]), a1[3]), cx, (uint32_t)G0)};
+    const float gb[2] = {pack_idx<LB>(fminf(fmin3(b0[0], b0[1], b0[2]), b0[3]), cx, (uint32_t)G0 + 4u),
+                         pack_idx<LB>(fminf(fmin3(b1[0], b1[1], b1[2]), b1[3]), cx, (uint32_t)G0 + 4u)};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int p = 2 * pp + e;
+      const float lo = fminf(ga[e], gb[e]), hi = fmaxf(ga[e], gb[e]);
+      if constexpr (FIRST) {
+        m1[p] = lo;
+        m2[p] = hi;
+      } else {
+        m2[p] = fmin3(m2[p], hi, fmaxf(m1[p], lo));
+        m1[p] = fminf(m1[p], lo);
+      }
+    }
+  }
+}
+
 // One warp-tile: grouped screen, exact recompute of the winning group, flags,
 // labels and exact sums.  FULL: all 256 points exist (no bounds checks).
-template <int D, bool FULL>
+// KG: groups of 4 centroids (kpad / 4) when fixed at compile time, else 0.
+template <int D, int KG, bool CT, bool FULL>
 __device__ __forceinline__ void process_tile(const FastArgs& a, FastSmem<D>& sm, const FastCtx& cx,
                                              const unsigned long long* s2, const float* xcur, int64_t base,
                                              int m, int lane, uint32_t* wmine, uint32_t* q, int& qn) {
   constexpr int DP = D + 1, WIN = 2 * D + 1, GS = FastSmem<D>::GS;
+  constexpr int LB = KG == 2 ? 3 : KG == 4 ? 4 : KG == 8 ? 5 : KG == 16 ? 6 : 0;
+  static_assert(KG == 0 || LB > 0, "compile-time group counts: 2, 4, 8, 16");
   // this lane's points: base + g*128 + 4*lane + q, g in {0,1}, q in 0..3;
   // pair pp holds points 2pp, 2pp+1.  X = x~ = fl(x - s) per pair.
   unsigned long long X[D][kPts / 2];
@@ -306,139 +446,128 @@ __device__ __forceinline__ void process_tile(const FastArgs& a, FastSmem<D>& sm,
       X[j][2 * g] = fsub2(v.x, s2[j]);
       X[j][2 * g + 1] = fsub2(v.y, s2[j]);
     }
-  // A = ||x~||^2 exactly as the data scan that bounds it: x0*x0, then FMAs.
-  float Ap[kPts];
-#pragma unroll
-  for (int pp = 0; pp < kPts / 2; ++pp) {
-    unsigned long long a2 = ffma2(X[0][pp], X[0][pp], 0ull);
-#pragma unroll
-    for (int j = 1; j < D; ++j) a2 = ffma2(X[j][pp], X[j][pp], a2);
-    unpack2(a2, Ap[2 * pp], Ap[2 * pp + 1]);
-  }
-
-  // Grouped screen: per group of 4 centroids only the group minimum of the
-  // raw r values is kept; the top-2 runs over groups, packed with the
-  // group's first index.
+  // Grouped screen over pairs of groups (kpad is a multiple of 8).
   float m1[kPts], m2[kPts];
+  if constexpr (CT) {
+    static_assert(KG > 0, "the constant-bank screen needs a compile-time group count");
+    screen_pair_ct<D, LB, true>(0, X, cx, m1, m2);
 #pragma unroll
-  for (int p = 0; p < kPts; ++p) { m1[p] = 3.0e38f; m2[p] = 3.0e38f; }
-#pragma unroll 1
-  for (int g4 = 0; g4 < cx.kpad; g4 += 4) {
-    const unsigned long long* tr = sm.tab + (size_t)g4 * DP;
-    unsigned long long T[4][DP];
-    if constexpr (D <= 3) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int j = 0; j < DP; ++j) T[c][j] = tr[c * DP + j];
+    for (int gp = 1; gp < KG / 2; ++gp) screen_pair_ct<D, LB, false>(8 * gp, X, cx, m1, m2);
+  } else {
+    {
+      float ga[kPts], gb[kPts];
+      screen_group<D, LB>(sm.tab, X, 0u, cx, ga);
+      screen_group<D, LB>(sm.tab + 4 * DP, X, 4u, cx, gb);
+      top2_pair<true>(m1, m2, ga, gb);
     }
-#pragma unroll
-    for (int pp = 0; pp < kPts / 2; ++pp) {
-      if constexpr (D > 3) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int j = 0; j < DP; ++j) T[c][j] = tr[c * DP + j];
-      }
-      float v0[4], v1[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        unsigned long long r = T[c][D];
-#pragma unroll
-        for (int j = 0; j < D; ++j) r = ffma2(X[j][pp], T[c][j], r);
-        unpack2(r, v0[c], v1[c]);
-      }
-      const float gm0 = fminf(fmin3(v0[0], v0[1], v0[2]), v0[3]);
-      const float gm1 = fminf(fmin3(v1[0], v1[1], v1[2]), v1[3]);
-      top2_one(m1[2 * pp], m2[2 * pp], __uint_as_float(imad(__float_as_uint(gm0), cx.mul, (uint32_t)g4)));
-      top2_one(m1[2 * pp + 1], m2[2 * pp + 1], __uint_as_float(imad(__float_as_uint(gm1), cx.mul, (uint32_t)g4)));
+  }
+  if constexpr (CT) {
+  } else if constexpr (KG > 0) {
+#pragma unroll kGpUnroll
+    for (int gp = 1; gp < KG / 2; ++gp) {
+      float ga[kPts], gb[kPts];
+      screen_group<D, LB>(sm.tab + (size_t)(8 * gp) * DP, X, 8u * gp, cx, ga);
+      screen_group<D, LB>(sm.tab + (size_t)(8 * gp + 4) * DP, X, 8u * gp + 4u, cx, gb);
+      top2_pair<false>(m1, m2, ga, gb);
+    }
+  } else {
+#pragma unroll 1
+    for (int g8 = 8; g8 < cx.kpad; g8 += 8) {
+      float ga[kPts], gb[kPts];
+      screen_group<D, 0>(sm.tab + (size_t)g8 * DP, X, (uint32_t)g8, cx, ga);
+      screen_group<D, 0>(sm.tab + (size_t)(g8 + 4) * DP, X, (uint32_t)g8 + 4u, cx, gb);
+      top2_pair<false>(m1, m2, ga, gb);
     }
   }
 
   // Epilogue: the winning group is recomputed exactly (the same FMA chain,
-  // two centroids per FFMA2) for the winner's index and the group's own
-  // second value; flags and labels follow.
+  // two centroids per FFMA2), its values packed with the index within the
+  // group; the label, the runner-up and the flag follow.
+  // bin[p]: the label, or k (the discard bin of the sums) for a flagged or
+  // padding point; a flagged point's label is written by the re-check.
   int lab[kPts];
   uint32_t fbits = 0u, dbits = 0u;  // flagged; not accumulated here
+  float Ap[2];
 #pragma unroll
   for (int p = 0; p < kPts; ++p) {
-    float xt[D];
+    if ((p & 1) == 0) {
+      // A = ||x~||^2 exactly as the data scan that bounds it: x0*x0, then FMAs.
+      unsigned long long a2 = ffma2(X[0][p >> 1], X[0][p >> 1], 0ull);
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-      float lo, hi;
-      unpack2(X[j][p >> 1], lo, hi);
-      xt[j] = (p & 1) ? hi : lo;
+      for (int j = 1; j < D; ++j) a2 = ffma2(X[j][p >> 1], X[j][p >> 1], a2);
+      unpack2(a2, Ap[0], Ap[1]);
     }
-    const uint32_t gsel = __float_as_uint(m1[p]) & cx.kmask;
+    const uint32_t gsel = __float_as_uint(m1[p]) & cx.kmask;  // the group's first index
     const ulonglong2* gt = reinterpret_cast<const ulonglong2*>(sm.gtab + (size_t)(gsel >> 2) * GS);
-    const ulonglong2 nv = gt[D];
-    unsigned long long rA = nv.x, rB = nv.y;
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      const ulonglong2 cv = gt[j];
-      const unsigned long long xx = dup2(xt[j]);
-      rA = ffma2(xx, cv.x, rA);
-      rB = ffma2(xx, cv.y, rB);
-    }
     float r0, r1, r2, r3;
-    unpack2(rA, r0, r1);
-    unpack2(rB, r2, r3);
-    const float w0 = __uint_as_float(imad(__float_as_uint(r0), cx.mul, gsel));
-    const float w1_ = __uint_as_float(imad(__float_as_uint(r1), cx.mul, gsel + 1u));
-    const float w2_ = __uint_as_float(imad(__float_as_uint(r2), cx.mul, gsel + 2u));
-    const float w3 = __uint_as_float(imad(__float_as_uint(r3), cx.mul, gsel + 3u));
-    const float lo01 = fminf(w0, w1_), hi01 = fmaxf(w0, w1_);
-    const float lo23 = fminf(w2_, w3), hi23 = fmaxf(w2_, w3);
+    {
+      const ulonglong2 nv = gt[D];
+      unsigned long long rA = nv.x, rB = nv.y;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float lo, hi;
+        unpack2(X[j][p >> 1], lo, hi);
+        const unsigned long long xx = dup2((p & 1) ? hi : lo);
+        const ulonglong2 cv = gt[j];
+        rA = ffma2(xx, cv.x, rA);
+        rB = ffma2(xx, cv.y, rB);
+      }
+      unpack2(rA, r0, r1);
+      unpack2(rB, r2, r3);
+    }
+    const float w0 = pack_idx<LB>(r0, cx, 0u), w1 = pack_idx<LB>(r1, cx, 1u);
+    const float w2 = pack_idx<LB>(r2, cx, 2u), w3 = pack_idx<LB>(r3, cx, 3u);
+    const float lo01 = fminf(w0, w1), hi01 = fmaxf(w0, w1);
+    const float lo23 = fminf(w2, w3), hi23 = fmaxf(w2, w3);
     const float best = fminf(lo01, lo23);
-    const float sec = fminf(fmin3(fmaxf(lo01, lo23), hi01, hi23), m2[p]);
-    const uint32_t u1 = __float_as_uint(best), u2 = __float_as_uint(sec);
-    lab[p] = (int)(u1 & cx.kmask);
-    const uint32_t b1 = u1 >> cx.L, b2 = u2 >> cx.L;
-    const float gap = (float)(int)(b2 - b1);
-    const float w2u = (float)(int)(b2 - cx.bitsM_low);
-    const float T = cx.thr_c0 + Ap[p] * cx.thr_cA2 + cx.tau * w2u;
+    const float sec = fmin3(fmaxf(lo01, lo23), fminf(hi01, hi23), m2[p]);
+    lab[p] = (int)(gsel | (__float_as_uint(best) & 3u));
+    const float v1 = unpack_val<LB>(best, cx), v2 = unpack_val<LB>(sec, cx);
+    const float T = fmaf(cx.tau, v2 - cx.M, fmaf(Ap[p & 1], cx.cA, cx.c0));
+    bool f = !(v2 - v1 > T);
     // a label outside 0..K-1 (only a padding centroid could give one) is
     // never trusted: the point goes to the re-check
-    bool f = !(gap > T) || lab[p] >= cx.k;
-    bool dis = f;
-    if constexpr (!FULL) {
-      const bool valid = base + (p >> 2) * kGS + 4 * lane + (p & 3) < a.n;
-      f = f && valid;
-      dis = dis || !valid;
-    }
-    fbits |= (f ? 1u : 0u) << p;
-    dbits |= (dis ? 1u : 0u) << p;
+    if (cx.k < cx.kpad) f = f || lab[p] >= cx.k;
+    bool valid = true;
+    if constexpr (!FULL) valid = base + (p >> 2) * kGS + 4 * lane + (p & 3) < a.n;
+    fbits |= ((f && valid) ? 1u : 0u) << p;
+    dbits |= ((f || !valid) ? 1u : 0u) << p;
   }
   if (__any_sync(0xffffffffu, fbits != 0u)) {
+    const int nf = __popc(fbits);
+    int incl = nf;
 #pragma unroll
-    for (int p = 0; p < kPts; ++p) {
-      const bool f = (fbits >> p) & 1u;
-      const unsigned bm = __ballot_sync(0xffffffffu, f);
-      if (f) {
-        const int off = (p >> 2) * kGS + 4 * lane + (p & 3);
-        q[qn + __popc(bm & ((1u << lane) - 1u))] = (uint32_t)(m << 8) | (uint32_t)off;
-      }
-      qn += __popc(bm);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
+    int at = qn + incl - nf;
+    for (uint32_t fb = fbits; fb; fb &= fb - 1u) {
+      const int p = __ffs(fb) - 1;
+      q[at++] = (uint32_t)(m << 8) | (uint32_t)((p >> 2) * kGS + 4 * lane + (p & 3));
+    }
+    qn += __shfl_sync(0xffffffffu, incl, 31);
   }
   // labels (flagged points are overwritten by the re-check)
+  if (a.store_labels) {
 #pragma unroll
-  for (int g = 0; g < kNG; ++g) {
-    const int64_t i0 = base + g * kGS + 4 * lane;
-    if (!a.store_labels) break;
-    if (a.labels8) {
-      if constexpr (FULL) {
-        *reinterpret_cast<uchar4*>(a.labels8 + i0) = make_uchar4((unsigned char)lab[4 * g], (unsigned char)lab[4 * g + 1],
-                                                                 (unsigned char)lab[4 * g + 2], (unsigned char)lab[4 * g + 3]);
+    for (int g = 0; g < kNG; ++g) {
+      const int64_t i0 = base + g * kGS + 4 * lane;
+      if (a.labels8) {
+        if constexpr (FULL) {
+          const uint32_t w = __byte_perm(__byte_perm(lab[4 * g], lab[4 * g + 1], 0x0040),
+                                         __byte_perm(lab[4 * g + 2], lab[4 * g + 3], 0x0040), 0x5410);
+          *reinterpret_cast<uint32_t*>(a.labels8 + i0) = w;
+        } else {
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) if (i0 + qq < a.n) a.labels8[i0 + qq] = (uint8_t)lab[4 * g + qq];
+        }
+      } else if constexpr (FULL) {
+        *reinterpret_cast<int4*>(a.labels + i0) = make_int4(lab[4 * g], lab[4 * g + 1], lab[4 * g + 2], lab[4 * g + 3]);
       } else {
 #pragma unroll
-        for (int qq = 0; qq < 4; ++qq) if (i0 + qq < a.n) a.labels8[i0 + qq] = (uint8_t)lab[4 * g + qq];
+        for (int qq = 0; qq < 4; ++qq) if (i0 + qq < a.n) a.labels[i0 + qq] = lab[4 * g + qq];
       }
-    } else if constexpr (FULL) {
-      *reinterpret_cast<int4*>(a.labels + i0) = make_int4(lab[4 * g], lab[4 * g + 1], lab[4 * g + 2], lab[4 * g + 3]);
-    } else {
-#pragma unroll
-      for (int qq = 0; qq < 4; ++qq) if (i0 + qq < a.n) a.labels[i0 + qq] = lab[4 * g + qq];
     }
   }
   // Exact sums: limb splits on FADD2 pairs, then 32-bit shared atomics into
@@ -462,8 +591,8 @@ __device__ __forceinline__ void process_tile(const FastArgs& a, FastSmem<D>& sm,
       }
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        const int bin = ((dbits >> (p0 + e)) & 1u) ? cx.k : lab[p0 + e];
-        uint32_t* wb = wmine + bin * WIN;
+        const int bn = ((dbits >> (p0 + e)) & 1u) ? cx.k : lab[p0 + e];
+        uint32_t* wb = wmine + bn * WIN;
         atomicAdd(&wb[0], 1u);
 #pragma unroll
         for (int j = 0; j < D; ++j) {
@@ -474,7 +603,7 @@ __device__ __forceinline__ void process_tile(const FastArgs& a, FastSmem<D>& sm,
     }
 }
 
-template <int D>
+template <int D, int KG, bool CT>
 __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs a) {
   constexpr int DP = D + 1, WIN = 2 * D + 1, GS = FastSmem<D>::GS;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -482,7 +611,7 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
   const int nbuf = a.nwin == 1 ? 1 : 2;
   FastSmem<D> sm(smraw, a.kpad, a.k, a.nwin, nbuf);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int k = a.k, kpad = a.kpad;
+  const int k = a.k, kpad = KG > 0 ? 4 * KG : a.kpad;
 
   const IterConst ic = *a.ic;
   const DataConst dc = *a.dc;
@@ -516,8 +645,16 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
   __syncthreads();
 
   FastCtx cx;
-  cx.mul = ic.mul; cx.L = (uint32_t)ic.L; cx.kmask = ic.mul - 1u; cx.bitsM_low = ic.bitsM_low;
-  cx.thr_c0 = ic.thr_c0; cx.thr_cA2 = ic.thr_cA + ic.tau * ic.G; cx.tau = ic.tau;
+  cx.L = (uint32_t)ic.L; cx.mul = ic.mul; cx.kmask = ic.mul - 1u;
+  cx.ehi = __float_as_uint(ic.M) >> (32 - ic.L);
+  cx.M = ic.M;
+  {
+    // ulp of the binade [2^eM, 2^(eM+1)) that holds every r: exact scaling
+    const float ulp = __uint_as_float(__float_as_uint(ic.M) & 0x7f800000u) * 0x1p-23f;
+    cx.c0 = ic.thr_c0 * ulp;
+    cx.cA = (ic.thr_cA + ic.tau * ic.G) * ulp;
+  }
+  cx.tau = ic.tau;
   cx.chi2 = dup2(dc.C_hi); cx.clo2 = dup2(dc.C_lo);
   cx.k = k; cx.kpad = kpad;
   int qn = 0, nflag = 0, n64 = 0, since_flush = 0;
@@ -532,9 +669,9 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
     if (nbuf == 2 && tile + wtot < ntiles)
       prefetch_tile<D>(a, xb + ((m + 1) & 1) * D * kWarpTile, (int64_t)(tile + wtot) * kWarpTile, lane);
     if (base + kWarpTile <= a.n)
-      process_tile<D, true>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
+      process_tile<D, KG, CT, true>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
     else
-      process_tile<D, false>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
+      process_tile<D, KG, CT, false>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
     if (nbuf == 1 && tile + wtot < ntiles) prefetch_tile<D>(a, xb, (int64_t)(tile + wtot) * kWarpTile, lane);
     // 16 lanes x 8 points x 4 tiles (or 32 lanes x 8 points x 2 tiles): <= 512 additions per bin
     if (++since_flush == (nwin == 2 ? 4 : 2)) {
@@ -656,30 +793,63 @@ size_t fast_smem_bytes(int d, int kpad, int k, int nwin) {
   return (b + 15) & ~size_t(15);
 }
 
-template <int D>
-static cudaError_t launch_fast_d(int grid, size_t smem, cudaStream_t st, const FastArgs& a) {
-  auto fn = assign_fast_kernel<D>;
+template <int D, int KG, bool CT>
+static cudaError_t launch_fast_dk(int grid, size_t smem, cudaStream_t st, const FastArgs& a) {
+  auto fn = assign_fast_kernel<D, KG, CT>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if constexpr (CT) {
+    e = cudaMemcpyToSymbolAsync(c_screen_tab, a.tab2, (size_t)a.kpad * (D + 1) * sizeof(unsigned long long), 0,
+                                cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
   fn<<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int D>
-static int blocks_d(size_t smem) {
+template <int D, int KG, bool CT>
+static int blocks_dk(size_t smem) {
   int nb = 0;
-  cudaFuncSetAttribute(assign_fast_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, assign_fast_kernel<D>, kThreads, smem) != cudaSuccess)
+  cudaFuncSetAttribute(assign_fast_kernel<D, KG, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, assign_fast_kernel<D, KG, CT>, kThreads, smem) !=
+      cudaSuccess)
     return 1;
   return nb > 0 ? nb : 1;
 }
 
-int fast_blocks_per_sm(int d, size_t smem) {
+// Instantiations: the constant-bank screen (compile-time group count, fully
+// unrolled, shift packing) for 3-D data with K <= 32 in groups of 8; a
+// runtime loop over the shared-memory table otherwise.
+#define KM_FAST_DISPATCH(FN, D, CT_OK, ...)                           \
+  do {                                                                \
+    if constexpr (D == 3) {                                           \
+      if (kpad == 32) {                                               \
+        if (CT_OK) return FN<D, 8, true>(__VA_ARGS__);                \
+        return FN<D, 8, false>(__VA_ARGS__);                          \
+      }                                                               \
+    }                                                                 \
+    return FN<D, 0, false>(__VA_ARGS__);                              \
+  } while (0)
+
+template <int D>
+static int blocks_d(size_t smem, int kpad, bool ct) {
+  KM_FAST_DISPATCH(blocks_dk, D, ct, smem);
+}
+
+template <int D>
+static cudaError_t launch_fast_d(int grid, size_t smem, cudaStream_t st, const FastArgs& a) {
+  const int kpad = a.kpad;
+  KM_FAST_DISPATCH(launch_fast_dk, D, a.const_tab != 0, grid, smem, st, a);
+}
+
+bool fast_has_const_table(int d, int kpad) { return d == 3 && kpad == 32; }
+
+int fast_blocks_per_sm(int d, size_t smem, int kpad, bool ct) {
   switch (d) {
-    case 1: return blocks_d<1>(smem);
-    case 2: return blocks_d<2>(smem);
-    case 3: return blocks_d<3>(smem);
-    default: return blocks_d<4>(smem);
+    case 1: return blocks_d<1>(smem, kpad, ct);
+    case 2: return blocks_d<2>(smem, kpad, ct);
+    case 3: return blocks_d<3>(smem, kpad, ct);
+    default: return blocks_d<4>(smem, kpad, ct);
   }
 }
 

@@ -50,6 +50,7 @@ static_assert(kPts == 4 || kPts == 8, "points per lane");
 #endif
 constexpr int kWarpQueue = 320;     // flagged points queued per warp (drained above 64)
 constexpr int64_t kMaxPointsPerBlock = int64_t(1) << 19;
+constexpr int kConstTabWords = 64 * 5;  // constant-bank screen table: kpad <= 64, d + 1 <= 5 packed pairs
 
 // Per-dataset constants, fixed by km_set_points.
 struct DataConst {
@@ -115,6 +116,7 @@ struct FastArgs {
   int store_labels;                // 0: labels are not written (label policy "final")
   uint8_t* labels8;                // non-null: labels are written here as bytes (K <= 256), not to labels
   int ignore_done;                 // 1: run even after the stop flag (the final labels pass)
+  int const_tab;                   // 1: the screen reads the table from the constant bank (copied at launch)
 };
 
 struct GenericArgs {
@@ -301,7 +303,9 @@ cudaError_t launch_objective(const float* x, int64_t ld, int64_t n, int d, const
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_assign_fast(int d, int grid, size_t smem, cudaStream_t st, const FastArgs& a);
 size_t fast_smem_bytes(int d, int kpad, int k, int nwin);
-int fast_blocks_per_sm(int d, size_t smem);
+int fast_blocks_per_sm(int d, size_t smem, int kpad, bool ct);
+// The fused kernel has a constant-bank screen table for this shape.
+bool fast_has_const_table(int d, int kpad);
 cudaError_t launch_assign_generic(int grid, size_t smem, cudaStream_t st, const GenericArgs& a);
 size_t generic_smem_bytes(int d, int k);
 
