@@ -73,6 +73,29 @@ def test_predict_and_adam_match_oracle(km):
     net.close()
 
 
+def test_adam_several_steps_match_oracle(km):
+    """Five Adam steps on the kernel's own gradients of a fixed batch: the
+    moments and the bias correction at t = 1..5 against the FP64 oracle's
+    update rule applied to the same gradients."""
+    params, x, t = _case(6, B=2, S=256)
+    p32 = _params32(params)
+    net = km.SetNet(3, 16)
+    net.set_params(p32)
+    ref = osn.unflatten(p32.astype(np.float64), 3, 16)
+    state = {}
+    for step in range(5):
+        net.loss_grad(x, t)
+        g = osn.unflatten(net.grads().astype(np.float64), 3, 16)
+        net.adam(1e-3)
+        ref = osn.adam(ref, g, state, lr=1e-3)
+        got = osn.unflatten(net.params().astype(np.float64), 3, 16)
+        for n in osn.PARAM_NAMES:
+            assert np.allclose(got[n], ref[n], rtol=1e-5, atol=2e-6), (step, n)
+        # continue from the kernel's parameters (float32), as training does
+        ref = got
+    net.close()
+
+
 def test_training_is_deterministic(km):
     params, x, t = _case(4, B=4, S=256)
     p32 = _params32(params)
