@@ -218,7 +218,8 @@ km_status km_device_buffers(km_ctx* ctx, const float** points, int64_t* ld_out,
  * code running under an allocator that must not be entered after start-up, a
  * real-time loop that forbids allocation, or a host framework that owns every
  * device allocation).  Everything is caller-owned device memory: x (d x N SoA,
- * row stride ld >= N, finite float32), mu_in (K x d doubles), and the outputs
+ * row stride ld >= N, finite float32 with |x| < 2^99), mu_in (K x d doubles),
+ * and the outputs
  * labels (N int32), mu_out (K x d doubles, may not alias mu_in), counts
  * (K int64) and e2_out (one double: E^2 against mu_in).  Same results as
  * km_step: exact labels (FP64 re-decision of near ties, ties to the lowest k),
@@ -227,12 +228,18 @@ km_status km_device_buffers(km_ctx* ctx, const float** points, int64_t* ld_out,
  * Limits of the fixed scratch (a ~0.6 MB file-scope __device__ array that
  * every device loading the library holds until exit): K*(d+1) <= 256 and
  * N <= 304 * 2^19.  Larger sizes return KM_EINVAL with a message in errbuf
- * (errbuf may be NULL; errlen is its size in bytes).
+ * (errbuf may be NULL; errlen is its size in bytes).  The call returns before
+ * the data is read, so data outside the range above (a NaN, an infinity or
+ * |x| >= 2^99) cannot be reported by the status: the step then marks its
+ * outputs invalid instead -- every mu_out entry and *e2_out are NaN and every
+ * count is -1 (labels are in 0..K-1 but meaningless).
  *
  * The work is queued on `stream` (a cudaStream_t, NULL = legacy default
  * stream) and the call returns without synchronizing.  The first call on a
  * device looks up the scratch array's device address (once per device, with
- * that device current); make that first call before any stream capture.  All
+ * that device current, and once more after the device's context has been
+ * destroyed and re-created, e.g. by cudaDeviceReset); make that first call
+ * before any stream capture.  All
  * calls share the one scratch array, which keeps the last call's contents:
  * calls that overlap on the GPU (different streams, or devices sharing the
  * same context) race and give wrong results; serialize them. */

@@ -172,6 +172,15 @@ __global__ void __launch_bounds__(kNaThreads) na_reduce_kernel(const NaScratch* 
   __shared__ long long s_cnt[kNaMaxCols];
   __shared__ double s_red[kNaThreads];
   const int dp = d + 1, cols = k * dp, tid = threadIdx.x;
+  // Data the fixed-point grid cannot hold (a NaN, an infinity or |x| >= 2^99;
+  // 0x71000000 is the bit pattern of 2^99): every output is marked invalid.
+  if (!(sc->absmax_bits < 0x71000000u)) {
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int q = tid; q < k * d; q += blockDim.x) mu_out[q] = nan;
+    for (int c = tid; c < k; c += blockDim.x) counts[c] = -1;
+    if (tid == 0) *e2_out = nan;
+    return;
+  }
   for (int c = tid; c < k; c += blockDim.x) {
     long long nsum = 0;
     for (int g = 0; g < G; ++g) nsum += sc->partials[(size_t)g * cols + (size_t)c * dp + d];
@@ -209,6 +218,24 @@ __global__ void __launch_bounds__(kNaThreads) na_reduce_kernel(const NaScratch* 
 
 std::mutex g_na_mutex;
 void* g_na_ptr[kNaMaxDevices] = {};
+void* g_na_ctx[kNaMaxDevices] = {};  // the context the cached address belongs to
+
+// The calling thread's current CUDA context (a driver handle), looked up
+// through the runtime's driver entry point so that libcuda is not linked.
+void* na_current_context() {
+  using GetCurrent = int (*)(void**);
+  static GetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<GetCurrent>(f);
+  }();
+  void* ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
 
 km_status na_fail(char* errbuf, int32_t errlen, km_status s, const char* msg) {
   if (errbuf && errlen > 0) std::snprintf(errbuf, (size_t)errlen, "%s", msg);
@@ -241,15 +268,20 @@ extern "C" km_status km_lloyd_step_noalloc(const float* x, int64_t ld, int64_t n
     return na_fail(errbuf, errlen, KM_ECUDA, "km_lloyd_step_noalloc: device ordinal out of range");
   NaScratch* sc = nullptr;
   {
-    // Set-up, once per device with that device current: the host-side name of
-    // the array is only a stand-in, so its device address is looked up.
+    // Set-up, once per device (and again after the device's context was
+    // destroyed and re-created, e.g. by cudaDeviceReset, which reloads the
+    // module), with that device current: the host-side name of the array is
+    // only a stand-in, so its device address is looked up.
+    // (No context yet, or no way to ask: the address is looked up every time.)
+    void* ctx = na_current_context();
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
+    if (!g_na_ptr[dev] || ctx != g_na_ctx[dev] || !ctx) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_na_scratch);
       if (e != cudaSuccess || !p)
         return na_fail(errbuf, errlen, KM_ECUDA, "km_lloyd_step_noalloc: cudaGetSymbolAddress failed");
       g_na_ptr[dev] = p;
+      g_na_ctx[dev] = ctx;
     }
     sc = static_cast<NaScratch*>(g_na_ptr[dev]);
   }

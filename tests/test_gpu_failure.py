@@ -69,10 +69,18 @@ def test_allocation_failures_are_reported_and_freed(km):
                 g.close()
         return run
 
+    insts = synth.batch_instances(3, seed=7, n_lo=500, n_hi=3_000)
+
     def batch():
-        b = km.KMeansBatch(np.array([2000, 3000]), np.array([2, 3]), np.array([4, 5]))
+        # creation, points (with the range scans), starts, the tuner's trial
+        # launches, the graph-driven run and the objective: every allocation
+        # of a batch's life is walked
+        b = km.KMeansBatch([w["n"] for w in insts], [w["d"] for w in insts], [w["k"] for w in insts])
         try:
-            pass
+            b.set_points([w["x"] for w in insts])
+            b.set_init([w["mu0"] for w in insts])
+            b.run(5, 1e-6)
+            b.objective()
         finally:
             b.close()
 

@@ -239,30 +239,14 @@ def test_offset_k256_on_the_fused_kernel(km, oracle):
 
 
 @pytest.mark.slow
-def test_full_scale_offset_n2p27_sampled(km, oracle):
-    """N = 2^27, d = 3, K = 256, offset 1e4 at full size: one step's labels
-    on a 20,000-point sample equal the oracle's argmin, counts are the label
-    histogram and every centroid is the mean of its points (float64 sums of
-    the labels' groups here)."""
+def test_full_scale_lockstep_offset_n2p27(km, oracle):
+    """N = 2^27, d = 3, K = 256, every coordinate offset by 1e4, at full size
+    and in the benchmark's launch configuration: one step from the k-means++
+    start, every label and count equal to the oracle's, every centroid within
+    1e-6 of the oracle's centroid, E and E^2 within the stated bounds."""
     w = synth.workload("precision_offset_3d_n2p27_k256")
-    x, mu0 = w["x"], w["mu0"]
-    n = x.shape[1]
-    g = km.KMeans(n, 3, 256)
-    g.set_points(x)
-    g.set_init(mu0)
-    g.step()
-    z = g.labels()
-    sel = np.sort(np.random.default_rng(1).choice(n, 20_000, replace=False))
-    assert np.array_equal(z[sel], oracle.assign(np.ascontiguousarray(x[:, sel]), mu0))
-    cnt = g.counts()
-    assert np.array_equal(cnt, np.bincount(z, minlength=256)) and cnt.sum() == n
-    mu = g.centroids()
-    sums = np.stack([np.bincount(z, weights=x[j].astype(np.float64), minlength=256) for j in range(3)], axis=1)
-    for c in range(256):
-        ref = sums[c] / cnt[c] if cnt[c] else mu0[c]
-        assert np.linalg.norm(mu[c] - ref) <= 1e-6 * max(np.linalg.norm(ref), 1.0)
-    assert g.stats()["path"] == 1
-    g.close()
+    st = lockstep(km, oracle, w["x"], w["mu0"], steps=1)
+    assert st["path"] == 1
 
 
 @pytest.mark.parametrize("case", ["fused_2d", "fused_k256", "generic_d5"])
