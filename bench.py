@@ -35,6 +35,9 @@ if ROOT not in sys.path:
 METRIC = "point-centroid distance evals/s per Lloyd iter"
 UNIT = "evals/s"
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM per clock (2 flops each)
+# FP64 add or multiply lane-operations per SM per cycle, measured on GB300
+# (independent DADD and DMUL chains, 32 warps per SM, clock64 timing): 1.89.
+FP64_ADDMUL_PER_SM_CYCLE = 1.89
 
 
 def parse():
@@ -56,6 +59,11 @@ def parse():
                     help="operand type of the tensor-core distances (d = 64)")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batch workloads")
     ap.add_argument("--learned-count", type=int, default=6, help="held-out mixtures of the learned-init workload")
+    ap.add_argument("--no-ttc", dest="ttc", action="store_false",
+                    help="skip the time-to-converge records of the default line")
+    ap.add_argument("--batch-ttc", type=int, default=256,
+                    help="default line: instances of the batch recipe (the first ones) run to convergence "
+                         "batched and one after another (0: skip)")
     ap.add_argument("--plain-every", type=int, default=1,
                     help="batch workloads: time plain km_run on every m-th instance (scaled up)")
     return ap.parse_args()
@@ -326,32 +334,80 @@ def run_ours(args, ws, rank, local):
     ms_step = total_ms / K
     value = whole_job_value(n, k, K, ws, total_ms)
     stats = g.stats()  # of the last timed step
+    g.close()  # the next contexts take over the device's constant-bank screen table
 
-    # end to end through the public API with host buffers (pinned)
+    # end to end through the public API with host buffers (pinned); each
+    # phase timed on the host with the stream drained at its end
     xp = torch.from_numpy(x).pin_memory()
     lab_out = torch.empty(n, dtype=torch.uint8 if lb == 1 else torch.int32).pin_memory()
-    e2e_times = []
+    e2e_times, phases = [], []
     g2 = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy, tc_operands=args.tc_operands,
                    label_bytes=lb)
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        g2.set_points(xp)
+        g2.set_points(xp)  # host-to-device copy, then the range scans
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
         g2.set_init(mu0)
         g2.step()
         if args.label_policy == "final":
             g2.write_labels()
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
         g2.labels_host_into(lab_out)
-        dt = time.perf_counter() - t0
+        t3 = time.perf_counter()
         if i:
-            e2e_times.append(dt)
+            e2e_times.append(t3 - t0)
+            phases.append((t1 - t0, t2 - t1, t3 - t2))
     g2.close()
     if e2e_times:
         e2e_s = statistics.median(e2e_times)
+        # the bare host-to-device copy of the same pinned bytes, to split
+        # set_points into the copy and the scans
+        xd = torch.empty_like(xp, device=dev)
+        cp = []
+        for _ in range(3):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            xd.copy_(xp, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            cp.append(time.perf_counter() - t0)
+        del xd
+        h2d_ms = 1e3 * min(cp)
+        ph = [statistics.median(v) * 1e3 for v in zip(*phases)]
         e2e = {"value": n * k / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * d * 4 + k * d * 8,
-               "d2h_bytes_per_step": n * lb + 16}
+               "d2h_bytes_per_step": n * lb + 16, "ms_per_step": 1e3 * e2e_s,
+               "breakdown_ms": {"set_points": ph[0], "of_which_h2d_copy": h2d_ms,
+                                "of_which_range_scans": max(0.0, ph[0] - h2d_ms),
+                                "set_init_step": ph[1], "labels_d2h": ph[2]},
+               "h2d_gbs": n * d * 4 / (h2d_ms / 1e3) / 1e9}
     else:
         e2e = None
+
+    # time to converge (the metric's second half): km_run from the same start,
+    # tol 1e-6, at most 300 steps, points resident, graph-driven loop
+    ttc = None
+    if args.ttc:
+        g3 = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy, tc_operands=args.tc_operands,
+                       label_bytes=lb)
+        g3.set_points(xt, borrow=True)
+        ttc_runs = []
+        for rep in range(2):  # the first run also builds the context's step graph
+            g3.set_init(mu0)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            r = g3.run(300, 1e-6, want_labels=False)
+            torch.cuda.synchronize(dev)
+            ttc_runs.append((time.perf_counter() - t0, r))
+        wall, r = ttc_runs[1]
+        ttc = {"wall_ms": 1e3 * wall, "wall_ms_first_run": 1e3 * ttc_runs[0][0], "iters": r["iters"],
+               "converged": bool(r["converged"]), "E": r["E"], "objective": g3.objective(),
+               "ms_per_iter": 1e3 * wall / max(1, r["iters"]), "tol": 1e-6, "max_iter": 300,
+               "evals_per_s": n * k * r["iters"] / wall,
+               "note": "km_run from the same k-means++ start; wall clock of the call (second run: the step "
+                       "graph already built); centroids copied out, labels left on the device"}
+        g3.close()
 
     pk, src = peaks()
     mhz = float(pk.get("sm_max_mhz", 2070.0))
@@ -387,7 +443,8 @@ def run_ours(args, ws, rank, local):
            "config": {"workload": args.workload, "n": n, "d": d, "k": k,
                       "init": "k-means++ on a 2^20-point subsample" if "n1e8" in args.workload or "n2p27" in args.workload
                               else "seeded distinct points",
-                      "l2": "points 1.2 GB > 129 MB L2: no flush needed" if n * d * 4 > 129e6 else "L2-resident",
+                      "l2": ("points %.2f GB > 129 MB L2: no flush needed" % (n * d * 4 / 1e9)) if n * d * 4 > 129e6
+                            else "L2-resident",
                       "parallelism": "single" if ws == 1 else f"replicas{ws}",
                       "labels": "one pass after the last step (inside the timed region)" if final_pass
                                 else "written every step",
@@ -398,10 +455,12 @@ def run_ours(args, ws, rank, local):
            "flagged_per_step": stats["flagged"], "fp64_decided_per_step": stats["fp64_decided"],
            "overflowed_per_step": stats["overflowed"],
            "path": {1: "fused FFMA2", 2: "generic",
-                    3: f"tcgen05 {args.tc_operands.upper()} GEMM-form"}.get(stats["path"])}
+                    3: f"tcgen05 {args.tc_operands.upper()} GEMM-form"}.get(stats["path"]),
+           "time_to_converge": ttc}
+    if args.ttc and args.batch_ttc > 0 and ws == 1:
+        out["batch_time_to_converge"] = batch_ttc(args.batch_ttc, dev)
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
-    g.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -424,6 +483,55 @@ def gen_batch(count, seed=0):
     jobs = [(i, int(ns[i]), int(ds[i]), int(ks[i])) for i in range(count)]
     with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
         return pool.map(_gen_instance, jobs, chunksize=8)
+
+
+def batch_ttc(count, dev):
+    """Time to converge of the first `count` instances of the batch recipe
+    (tol 1e-6, max 300): one KMeansBatch run (launch shape from the tuner,
+    tuning not timed) against the same instances run one after another with
+    plain km_run (each context's step graph already built: its second run is
+    timed)."""
+    import numpy as np
+    import torch
+    import paper_2405_12052_gb300 as km
+    t0 = time.perf_counter()
+    insts = gen_batch(count)
+    gen_s = time.perf_counter() - t0
+    ns = np.array([w["n"] for w in insts]); ds = np.array([w["d"] for w in insts]); ks = np.array([w["k"] for w in insts])
+    flat = np.concatenate([w["x"].reshape(-1) for w in insts])
+    mus = np.concatenate([w["mu0"].reshape(-1) for w in insts])
+    b = km.KMeansBatch(ns, ds, ks)
+    b.set_points(torch.from_numpy(flat).to(dev))
+    b.set_init(mus)
+    tile, thr = b.tune()
+    b.set_init(mus)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    r = b.run(300, 1e-6, want_labels=False)
+    torch.cuda.synchronize(dev)
+    batch_s = time.perf_counter() - t0
+    mu_b = b.split_centroids(r["centroids"])
+    iters = r["iters"].astype(np.int64)
+    b.close()
+    plain_s, same = 0.0, True
+    for i, w in enumerate(insts):
+        g = km.KMeans(w["n"], w["d"], w["k"])
+        g.set_points(w["x"])
+        g.set_init(w["mu0"])
+        g.run(300, 1e-6, want_labels=False)  # builds the step graph
+        g.set_init(w["mu0"])
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        rr = g.run(300, 1e-6, want_labels=False)
+        plain_s += time.perf_counter() - t1
+        same = same and rr["iters"] == int(iters[i]) and np.array_equal(rr["centroids"], mu_b[i])
+        g.close()
+    return {"instances": count, "points": int(ns.sum()), "batch_s": batch_s, "plain_sequential_s": plain_s,
+            "speedup": plain_s / batch_s, "same_results": bool(same), "iters_total": int(iters.sum()),
+            "iters_max": int(iters.max()), "converged": int(r["converged"].sum()),
+            "evals_per_s": float(np.sum(ns * ks * iters)) / batch_s, "autotune": [tile, thr],
+            "generate_s": gen_s,
+            "recipe": "the first instances of the batch workload (sizes from seed 0, instance i seeded 1000 + i)"}
 
 
 def run_batch(args, ws, rank, local):
@@ -634,8 +742,16 @@ def run_kmeanspp(args, ws, rank, local):
     clk = clocks.stop()
     g.close()
     t = statistics.median(times)
-    flops = 3.0 * d * n * k  # per point and round: d FP64 subtractions, squares and adds
-    ach = flops / t / 1e12
+    # Per point and round the oracle's expression takes d FP64 subtractions,
+    # d products and d additions (unfused: fusing would change the sums and
+    # hence the picks).  Its ceiling is the FP64 add/multiply issue rate:
+    # FP64_ADDMUL_PER_SM_CYCLE lane-operations per SM cycle, measured on GB300
+    # with independent DADD/DMUL chains timed by clock64().
+    ops = 3.0 * d * n * k
+    mhz = float(peaks()[0].get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = FP64_ADDMUL_PER_SM_CYCLE * sms * mhz * 1e6 / 1e12
+    ach = ops / t / 1e12
     out = {"metric": METRIC, "value": n * k / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -643,9 +759,11 @@ def run_kmeanspp(args, ws, rank, local):
                       "step": "one k-means++ seeding (K rounds), host wall time around the call",
                       "parallelism": "single"},
            "clocks": clk, "e2e": None, "gpu_launches": 2 * k - 1,
-           "roofline": {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+           "roofline": {"bound": "alu", "achieved": ach, "peak": peak_ops, "unit": "Tops/s (FP64 add/mul)",
+                        "frac": ach / peak_ops,
                         "traffic": None, "kernel": "kpp_d2_kernel + kpp_pick_kernel",
-                        "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak); 3 N K d FP64 flops "
+                        "peak_source": f"measured FP64 DADD/DMUL issue rate, {FP64_ADDMUL_PER_SM_CYCLE} lane-ops "
+                                       f"per SM cycle x {sms} SMs x {mhz:.0f} MHz; 3 N K d FP64 operations "
                                        "per seeding",
                         "hbm_frac_of_measured": (n * (4 * d + 16) * k / t / 1e9) / float(peaks()[0].get("hbm_gbs", 6800.0))}}
     print(json.dumps(out), flush=True)
