@@ -166,6 +166,42 @@ km_status km_assign_async(km_ctx* ctx);
 km_status km_update_async(km_ctx* ctx);
 km_status km_sync(km_ctx* ctx, int32_t* iters_out, double* e_out, int32_t* done_out);
 
+/* Sharded steps: the points split over R contexts (one per process or GPU,
+ * each holding a contiguous or any other disjoint part), with the caller
+ * exchanging a small table per step -- the paper's OpenMP scheme, where each
+ * thread's local sums are merged before the master thread divides (section
+ * "Parallel Lloyd's algorithm", "Using OpenMP"), with an all-gather in place
+ * of the critical section.
+ *
+ * Set-up: after km_set_points on every shard, read each shard's fixed-point
+ * grid exponent with km_grid_exponent, take the maximum over the shards and
+ * give it to every shard with km_set_grid_exponent (the exponent of a single
+ * context over all points is that maximum).  Then km_set_init with the same
+ * centroids on every shard, and km_begin as for the asynchronous pieces.
+ *
+ * Each step on each shard: km_assign_async; km_shard_totals writes this
+ * shard's column totals -- for every centre k and column j (0..d-1 the
+ * coordinate sums on the fixed-point grid, d the count) one exact int128 as
+ * two int64 words, low word first: K * (d+1) * 2 int64 in total, row-major
+ * [k][j][word]; the caller all-gathers the R tables in rank order
+ * (R * K * (d+1) * 2 int64) and passes them to km_shard_update, which adds
+ * them in rank order (exact integers), divides, forms E, applies the stop
+ * rule and prepares the next step.  Because every sum is an exact integer
+ * and the labels are exact, every shard's centroids, counts (global) and E
+ * are bit-identical to one context over all points, and each shard's labels
+ * are that context's labels of its points.
+ *
+ * mem: KM_HOST (host arrays; the call synchronizes) or KM_DEVICE_COPY
+ * (device arrays of the context's device, used on the context's stream
+ * without synchronizing).  The FP32 paths only (KM_EINVAL on the
+ * tensor-core path).  km_set_grid_exponent returns KM_EINVAL below the
+ * exponent the shard's own points need or above 100, KM_ESTATE before
+ * km_set_points. */
+km_status km_grid_exponent(km_ctx* ctx, int32_t* ex_out);
+km_status km_set_grid_exponent(km_ctx* ctx, int32_t ex);
+km_status km_shard_totals(km_ctx* ctx, int64_t* totals_out, int32_t mem);
+km_status km_shard_update(km_ctx* ctx, const int64_t* tables, int32_t ranks, int32_t mem);
+
 /* The stream the context queues its work on (a cudaStream_t). */
 void* km_stream(km_ctx* ctx);
 

@@ -115,6 +115,14 @@ def lib(path: str | None = None):
     L.km_update_async.restype = st
     L.km_sync.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(f64), ctypes.POINTER(i32)]
     L.km_sync.restype = st
+    L.km_grid_exponent.argtypes = [P, ctypes.POINTER(i32)]
+    L.km_grid_exponent.restype = st
+    L.km_set_grid_exponent.argtypes = [P, i32]
+    L.km_set_grid_exponent.restype = st
+    L.km_shard_totals.argtypes = [P, P, i32]
+    L.km_shard_totals.restype = st
+    L.km_shard_update.argtypes = [P, P, i32, i32]
+    L.km_shard_update.restype = st
     L.km_stream.argtypes = [P]
     L.km_stream.restype = P
     L.km_lloyd_step_noalloc.argtypes = [P, i64, i64, i32, i32, P, P, P, P, P, P, ctypes.c_char_p, i32]
@@ -422,6 +430,32 @@ class KMeans:
         it, e, done = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()
         self._check(self._L.km_sync(self._h, ctypes.byref(it), ctypes.byref(e), ctypes.byref(done)))
         return dict(iters=it.value, E=e.value, done=bool(done.value))
+
+    # -- sharded steps (the points split over several contexts) --
+    def grid_exponent(self) -> int:
+        """The fixed-point grid exponent this context uses (km_grid_exponent)."""
+        ex = ctypes.c_int32()
+        self._check(self._L.km_grid_exponent(self._h, ctypes.byref(ex)))
+        return ex.value
+
+    def set_grid_exponent(self, ex: int):
+        """Use the shards' common (maximum) grid exponent."""
+        self._check(self._L.km_set_grid_exponent(self._h, int(ex)))
+
+    def shard_totals(self) -> np.ndarray:
+        """This shard's column totals after assign_async: (K*(d+1), 2) int64,
+        the int128 (low word, high word) of every column."""
+        out = np.empty((self.k * (self.d + 1), 2), dtype=np.int64)
+        self._check(self._L.km_shard_totals(self._h, out.ctypes.data, KM_HOST))
+        return out
+
+    def shard_update(self, tables):
+        """The update from the R shards' totals gathered in rank order:
+        an (R, K*(d+1), 2) int64 array (host)."""
+        t = np.ascontiguousarray(tables, dtype=np.int64)
+        if t.ndim != 3 or t.shape[1:] != (self.k * (self.d + 1), 2):
+            raise ValueError("tables must be (ranks, K*(d+1), 2) int64")
+        self._check(self._L.km_shard_update(self._h, t.ctypes.data, int(t.shape[0]), KM_HOST))
 
     @property
     def stream_handle(self) -> int:

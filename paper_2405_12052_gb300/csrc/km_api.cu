@@ -78,6 +78,11 @@ struct km_ctx {
   size_t fast_smem = 0;
   int nwin = 2;  // fused path: sum windows per warp
   bool const_tab = false;  // this context holds the device's constant-bank screen table
+  int grid_ex = 0;         // fixed-point grid exponent: |x| < 2^(grid_ex - 1), G0 = grid_ex - 44
+  int grid_ex_local = 0;   // the exponent this context's own points need
+  long long* shard_out = nullptr;  // [k][d+1][2] column totals (host-memory requests)
+  long long* shard_in = nullptr;   // [ranks][k][d+1][2] gathered totals (host-memory requests)
+  int shard_in_ranks = 0;
   int path = 0;  // 1 fused (d <= 4, K <= 256), 2 generic, 3 tensor cores (d = 64, K <= 1024)
   // tensor-core path
   void* xb = nullptr;
@@ -141,7 +146,8 @@ void free_all(km_ctx* c) {
                   c->ctil4, c->ctil, c->cnorm, c->shift, c->gen_bmax, c->dc, c->ic, c->ls,
                   c->scan, c->scan_bad, c->xb, c->xa_pt, c->xaos, c->cbf, c->nprime, c->gc,
                   c->ms_counts, c->ms_offsets, c->ms_cfirst, c->ms_cursor, c->ms_chunks, c->ms_nchunks,
-                  c->ms_chunk_sums, c->ms_perm, c->rescue_list, c->tie_list, c->rescue_count, c->ms_df2, c->bnorm};
+                  c->ms_chunk_sums, c->ms_perm, c->rescue_list, c->tie_list, c->rescue_count, c->ms_df2, c->bnorm,
+                  c->shard_out, c->shard_in};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -523,6 +529,7 @@ km_status km_set_points(km_ctx* c, const float* x, int64_t ld, int32_t layout, i
   hdc.A_max = ha;
   c->A_max = ha;
   c->G0 = hdc.G0;
+  c->grid_ex = c->grid_ex_local = ex;
   KM_CUDA(c, cudaMemcpyAsync(c->dc, &hdc, sizeof(hdc), cudaMemcpyHostToDevice, c->st));
   KM_CUDA(c, cudaStreamSynchronize(c->st));
   if (c->path == 3) {
@@ -759,6 +766,77 @@ km_status km_update_async(km_ctx* c) {
   km_status s = ready(c);
   if (s != KM_OK) return s;
   KM_CUDA(c, launch_update_all(c));
+  return KM_OK;
+}
+
+km_status km_grid_exponent(km_ctx* c, int32_t* ex_out) {
+  if (!c || !ex_out) return KM_EINVAL;
+  if (!c->have_points) return fail(c, KM_ESTATE, "km_set_points must come first");
+  *ex_out = c->grid_ex;
+  return KM_OK;
+}
+
+km_status km_set_grid_exponent(km_ctx* c, int32_t ex) {
+  if (!c) return KM_EINVAL;
+  if (!c->have_points) return fail(c, KM_ESTATE, "km_set_points must come first");
+  if (ex < c->grid_ex_local)
+    return fail(c, KM_EINVAL, "grid exponent below the one this context's points need (" +
+                                  std::to_string(c->grid_ex_local) + ")");
+  if (ex > 100) return fail(c, KM_EINVAL, "grid exponent above 100 (|x| >= 2^99)");
+  DataConst hdc{};
+  KM_CUDA(c, cudaMemcpyAsync(&hdc, c->dc, sizeof(hdc), cudaMemcpyDeviceToHost, c->st));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  hdc.G0 = ex - 44;
+  hdc.C_hi = std::ldexp(1.5f, ex + 1);
+  hdc.C_lo = std::ldexp(1.5f, ex - 21);
+  std::memcpy(&hdc.bits_C_hi, &hdc.C_hi, 4);
+  std::memcpy(&hdc.bits_C_lo, &hdc.C_lo, 4);
+  KM_CUDA(c, cudaMemcpyAsync(c->dc, &hdc, sizeof(hdc), cudaMemcpyHostToDevice, c->st));
+  KM_CUDA(c, cudaStreamSynchronize(c->st));
+  c->G0 = hdc.G0;
+  c->grid_ex = ex;
+  return KM_OK;
+}
+
+km_status km_shard_totals(km_ctx* c, int64_t* out, int32_t mem) {
+  km_status s = ready(c);
+  if (s != KM_OK) return s;
+  if (!out || (mem != KM_HOST && mem != KM_DEVICE_COPY)) return fail(c, KM_EINVAL, "bad output");
+  if (c->path == 3) return fail(c, KM_EINVAL, "sharded steps are for the FP32 paths (d <= 4 or any d off the tensor cores)");
+  const size_t words = (size_t)c->k * (c->d + 1) * 2;
+  long long* dst = reinterpret_cast<long long*>(out);
+  if (mem == KM_HOST) {
+    if (!c->shard_out) KM_CUDA(c, dalloc(&c->shard_out, words));
+    dst = c->shard_out;
+  }
+  KM_CUDA(c, launch_shard_totals(c->st, update_args(c), dst));
+  if (mem == KM_HOST) {
+    KM_CUDA(c, cudaMemcpyAsync(out, dst, words * sizeof(long long), cudaMemcpyDeviceToHost, c->st));
+    KM_CUDA(c, cudaStreamSynchronize(c->st));
+  }
+  return KM_OK;
+}
+
+km_status km_shard_update(km_ctx* c, const int64_t* tables, int32_t ranks, int32_t mem) {
+  km_status s = ready(c);
+  if (s != KM_OK) return s;
+  if (!tables || ranks < 1 || (mem != KM_HOST && mem != KM_DEVICE_COPY)) return fail(c, KM_EINVAL, "bad tables");
+  if (c->path == 3) return fail(c, KM_EINVAL, "sharded steps are for the FP32 paths (d <= 4 or any d off the tensor cores)");
+  const size_t words = (size_t)c->k * (c->d + 1) * 2;
+  const long long* src = reinterpret_cast<const long long*>(tables);
+  if (mem == KM_HOST) {
+    if (ranks > c->shard_in_ranks) {
+      if (c->shard_in) cudaFree(c->shard_in);
+      c->shard_in = nullptr;
+      c->shard_in_ranks = 0;
+      KM_CUDA(c, dalloc(&c->shard_in, words * ranks));
+      c->shard_in_ranks = ranks;
+    }
+    KM_CUDA(c, cudaMemcpyAsync(c->shard_in, tables, words * ranks * sizeof(long long), cudaMemcpyHostToDevice, c->st));
+    src = c->shard_in;
+  }
+  KM_CUDA(c, launch_shard_update(c->st, update_args(c), src, ranks));
+  if (mem == KM_HOST) KM_CUDA(c, cudaStreamSynchronize(c->st));  // the host tables may be reused at once
   return KM_OK;
 }
 

@@ -331,6 +331,10 @@ struct UpdateArgs {
 };
 cudaError_t launch_update(cudaStream_t st, const UpdateArgs& a);
 cudaError_t launch_prepare(cudaStream_t st, const UpdateArgs& a);  // tables from mu, no step
+// Sharded steps: this context's int128 column totals ([k][d+1][2] int64), and
+// the update from the totals of R shards gathered in rank order.
+cudaError_t launch_shard_totals(cudaStream_t st, const UpdateArgs& a, long long* out);
+cudaError_t launch_shard_update(cudaStream_t st, const UpdateArgs& a, const long long* tables, int ranks);
 
 // Data scan: per-coordinate min/max, absmax, non-finite count.
 cudaError_t launch_scan_range(const float* x, int64_t ld, int64_t n, int d, float* mn, float* mx,

@@ -160,53 +160,19 @@ __device__ void prepare_tables(const UpdateArgs& a, double* sB) {
 
 constexpr int kRedCols = 32, kRedRows = 8;
 
-__global__ void __launch_bounds__(kRedCols * kRedRows) reduce_update_kernel(UpdateArgs a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  double* sB = reinterpret_cast<double*>(smraw);  // [k] for the fused-path tables
-  __shared__ unsigned long long s_lo[kRedRows][kRedCols];
-  __shared__ long long s_hi[kRedRows][kRedCols];
-  __shared__ bool s_last;
-  __shared__ double s_red[kRedCols * kRedRows];
-  if (a.ls->done) return;
-  const int cols = a.k * (a.d + 1);
-  const int col = blockIdx.x * kRedCols + threadIdx.x;
-  const int tid = threadIdx.y * kRedCols + threadIdx.x;
-  {
-    unsigned long long lo = 0ull;
-    long long hi = 0ll;
-    if (col < cols) {
-      for (int g = blockIdx.y * kRedRows + threadIdx.y; g < a.G; g += gridDim.y * kRedRows)
-        add128(lo, hi, a.partials[(size_t)g * cols + col]);
-    }
-    s_lo[threadIdx.y][threadIdx.x] = lo;
-    s_hi[threadIdx.y][threadIdx.x] = hi;
-    __syncthreads();
-    if (threadIdx.y == 0 && col < cols) {
-      unsigned long long tl = 0ull;
-      long long th = 0ll;
-      for (int r = 0; r < kRedRows; ++r) add128p(tl, th, s_lo[r][threadIdx.x], s_hi[r][threadIdx.x]);
-      long long* out = a.s128 + ((size_t)blockIdx.y * cols + col) * 2;
-      out[0] = (long long)tl;
-      out[1] = th;
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    const unsigned int t = atomicAdd(&a.ls->ticket, 1u);
-    s_last = (t == gridDim.x * gridDim.y - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-
-  // Last block: fixed-order totals, divide, error, stop test, next tables.
-  const int k = a.k, d = a.d, dp = d + 1, RB = gridDim.y;
+// The last step of the update, given the int128 column totals of RB row
+// groups (the reduction's row blocks, or the shards of a sharded step) in
+// s128 [RB][k][d+1][2]: totals added in row-group order, one conversion to
+// FP64, the divide (an empty cluster keeps its centre), E^2 by a fixed-order
+// tree, the stop test and the next step's screen tables.
+__device__ void finish_update(const UpdateArgs& a, const long long* s128, int RB, double* sB, double* s_red,
+                              int tid) {
+  const int k = a.k, d = a.d, dp = d + 1, cols = k * dp;
   const int nth = kRedCols * kRedRows;
   int empty = 0;
   for (int c = tid; c < k; c += nth) {
     long long n = 0;
-    for (int rb = 0; rb < RB; ++rb) n += a.s128[((size_t)rb * cols + (size_t)c * dp + d) * 2];
+    for (int rb = 0; rb < RB; ++rb) n += s128[((size_t)rb * cols + (size_t)c * dp + d) * 2];
     a.counts[c] = n;
     empty += (n == 0);
   }
@@ -218,7 +184,7 @@ __global__ void __launch_bounds__(kRedCols * kRedRows) reduce_update_kernel(Upda
     unsigned long long tl = 0ull;
     long long th = 0ll;
     for (int rb = 0; rb < RB; ++rb) {
-      const long long* v = a.s128 + ((size_t)rb * cols + (size_t)c * dp + j) * 2;
+      const long long* v = s128 + ((size_t)rb * cols + (size_t)c * dp + j) * 2;
       add128p(tl, th, (unsigned long long)v[0], v[1]);
     }
     const long long n = a.counts[c];
@@ -262,6 +228,84 @@ __global__ void __launch_bounds__(kRedCols * kRedRows) reduce_update_kernel(Upda
   }
   __syncthreads();
   prepare_tables(a, sB);
+}
+
+
+__global__ void __launch_bounds__(kRedCols * kRedRows) reduce_update_kernel(UpdateArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sB = reinterpret_cast<double*>(smraw);  // [k] for the fused-path tables
+  __shared__ unsigned long long s_lo[kRedRows][kRedCols];
+  __shared__ long long s_hi[kRedRows][kRedCols];
+  __shared__ bool s_last;
+  __shared__ double s_red[kRedCols * kRedRows];
+  if (a.ls->done) return;
+  const int cols = a.k * (a.d + 1);
+  const int col = blockIdx.x * kRedCols + threadIdx.x;
+  const int tid = threadIdx.y * kRedCols + threadIdx.x;
+  {
+    unsigned long long lo = 0ull;
+    long long hi = 0ll;
+    if (col < cols) {
+      for (int g = blockIdx.y * kRedRows + threadIdx.y; g < a.G; g += gridDim.y * kRedRows)
+        add128(lo, hi, a.partials[(size_t)g * cols + col]);
+    }
+    s_lo[threadIdx.y][threadIdx.x] = lo;
+    s_hi[threadIdx.y][threadIdx.x] = hi;
+    __syncthreads();
+    if (threadIdx.y == 0 && col < cols) {
+      unsigned long long tl = 0ull;
+      long long th = 0ll;
+      for (int r = 0; r < kRedRows; ++r) add128p(tl, th, s_lo[r][threadIdx.x], s_hi[r][threadIdx.x]);
+      long long* out = a.s128 + ((size_t)blockIdx.y * cols + col) * 2;
+      out[0] = (long long)tl;
+      out[1] = th;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned int t = atomicAdd(&a.ls->ticket, 1u);
+    s_last = (t == gridDim.x * gridDim.y - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+
+  finish_update(a, a.s128, (int)gridDim.y, sB, s_red, tid);
+}
+
+// One block of kRedCols x kRedRows threads: the mean calculation from the
+// gathered column totals of R shards (rank order), as the last block above.
+__global__ void __launch_bounds__(kRedCols * kRedRows) shard_update_kernel(UpdateArgs a, const long long* tables,
+                                                                            int ranks) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sB = reinterpret_cast<double*>(smraw);
+  __shared__ double s_red[kRedCols * kRedRows];
+  if (a.ls->done) return;
+  finish_update(a, tables, ranks, sB, s_red, threadIdx.y * kRedCols + threadIdx.x);
+}
+
+// Column totals of this context's per-block partials: one int128 (two int64
+// words, low word first) per column of [k][d+1]; integer sums, so exact.
+__global__ void __launch_bounds__(kRedCols * kRedRows) shard_totals_kernel(UpdateArgs a, long long* out) {
+  __shared__ unsigned long long s_lo[kRedRows][kRedCols];
+  __shared__ long long s_hi[kRedRows][kRedCols];
+  const int cols = a.k * (a.d + 1);
+  const int col = blockIdx.x * kRedCols + threadIdx.x;
+  unsigned long long lo = 0ull;
+  long long hi = 0ll;
+  if (col < cols)
+    for (int g = threadIdx.y; g < a.G; g += kRedRows) add128(lo, hi, a.partials[(size_t)g * cols + col]);
+  s_lo[threadIdx.y][threadIdx.x] = lo;
+  s_hi[threadIdx.y][threadIdx.x] = hi;
+  __syncthreads();
+  if (threadIdx.y == 0 && col < cols) {
+    unsigned long long tl = 0ull;
+    long long th = 0ll;
+    for (int r = 0; r < kRedRows; ++r) add128p(tl, th, s_lo[r][threadIdx.x], s_hi[r][threadIdx.x]);
+    out[(size_t)col * 2] = (long long)tl;
+    out[(size_t)col * 2 + 1] = th;
+  }
 }
 
 __global__ void __launch_bounds__(256) prepare_kernel(UpdateArgs a) {
@@ -359,6 +403,22 @@ cudaError_t launch_update(cudaStream_t st, const UpdateArgs& a) {
     if (e != cudaSuccess) return e;
   }
   reduce_update_kernel<<<grid, block, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shard_totals(cudaStream_t st, const UpdateArgs& a, long long* out) {
+  const int cols = a.k * (a.d + 1);
+  shard_totals_kernel<<<(cols + kRedCols - 1) / kRedCols, dim3(kRedCols, kRedRows), 0, st>>>(a, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shard_update(cudaStream_t st, const UpdateArgs& a, const long long* tables, int ranks) {
+  const size_t smem = (size_t)(a.fast ? a.k : 0) * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(shard_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  shard_update_kernel<<<1, dim3(kRedCols, kRedRows), smem, st>>>(a, tables, ranks);
   return cudaGetLastError();
 }
 
