@@ -420,6 +420,30 @@ void km_setnet_destroy(km_setnet* net);
  * network's), KM_ENOMEM, KM_ECUDA. */
 km_status km_init_learned(km_ctx* ctx, km_setnet* net, int32_t sample_n, uint64_t seed, double* mu_out);
 
+/* Set transforms used around the network (test-time rotations of the
+ * sample, rotations of training sets): the network's error depends on the
+ * orientation of its input, so predictions for several rotated copies of
+ * one sample can be compared (section "The Lloyd's algorithm": the result
+ * depends on the initial centres).  All pointers are device memory of the
+ * current device; the work is queued on `stream` without synchronizing.
+ *   km_sets_mean: means_out[b][j] = the FP64 mean over s of x[b][s][j], for
+ *     B sets of S points of dimension d (1..3), set b at x + b * set_stride
+ *     (floats; 0 repeats one set), point s at offset s * d.
+ *   km_sets_rotate_f32 / _f64: out[b][s] = R_b (x[b][s] - c_b) + c_b, or
+ *     with R_b^T when transpose is non-zero; R is B x d x d row-major
+ *     doubles (the rotations are inputs: random numbers the caller draws),
+ *     c_b = center + b * center_stride (NULL: the origin); out is B x S x d
+ *     contiguous; arithmetic in FP64, one rounding to the output type.
+ * Errors: KM_EINVAL (null pointer, d outside 1..3, negative sizes),
+ *         KM_ECUDA. */
+km_status km_sets_mean(const float* x, int64_t set_stride, int32_t B, int32_t S, int32_t d, double* means_out,
+                       void* stream);
+km_status km_sets_rotate_f32(const float* x, int64_t set_stride, int32_t B, int32_t S, int32_t d, const double* R,
+                             const double* center, int64_t center_stride, int32_t transpose, float* out, void* stream);
+km_status km_sets_rotate_f64(const double* x, int64_t set_stride, int32_t B, int32_t S, int32_t d, const double* R,
+                             const double* center, int64_t center_stride, int32_t transpose, double* out,
+                             void* stream);
+
 /* Library version string and the sm architecture it was built for. */
 const char* km_version(void);
 

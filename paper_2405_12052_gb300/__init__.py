@@ -17,7 +17,8 @@ import re
 
 import numpy as np
 
-__all__ = ["KMeans", "KMeansBatch", "SetNet", "KMError", "lib", "header_symbols", "build", "LIB_PATH", "HEADER"]
+__all__ = ["KMeans", "KMeansBatch", "SetNet", "KMError", "lib", "header_symbols", "build", "LIB_PATH", "HEADER",
+           "sets_mean", "sets_rotate"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libkm.so")
@@ -115,6 +116,12 @@ def lib(path: str | None = None):
     L.km_update_async.restype = st
     L.km_sync.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(f64), ctypes.POINTER(i32)]
     L.km_sync.restype = st
+    L.km_sets_mean.argtypes = [P, i64, i32, i32, i32, P, P]
+    L.km_sets_mean.restype = st
+    L.km_sets_rotate_f32.argtypes = [P, i64, i32, i32, i32, P, P, i64, i32, P, P]
+    L.km_sets_rotate_f32.restype = st
+    L.km_sets_rotate_f64.argtypes = [P, i64, i32, i32, i32, P, P, i64, i32, P, P]
+    L.km_sets_rotate_f64.restype = st
     L.km_grid_exponent.argtypes = [P, ctypes.POINTER(i32)]
     L.km_grid_exponent.restype = st
     L.km_set_grid_exponent.argtypes = [P, i32]
@@ -758,3 +765,57 @@ class SetNet:
         out = np.empty((B, self.k, self.d), dtype=np.float64)
         self._check(self._L.km_setnet_predict(self._h, px, B, S, mx, out.ctypes.data))
         return out
+
+
+def _cuda_stream(t):
+    import torch
+    return torch.cuda.current_stream(t.device).cuda_stream
+
+
+def sets_mean(x, set_stride: int | None = None, sets: int | None = None):
+    """km_sets_mean on a CUDA float32 tensor x of B sets (B, S, d) -- or one
+    set (S, d) repeated `sets` times with set_stride 0.  Returns (B, d)
+    float64 means on the device."""
+    import torch
+    if x.dim() == 2:
+        x = x.unsqueeze(0)
+    x = x.contiguous()
+    B, S, d = x.shape
+    stride = S * d if set_stride is None else set_stride
+    B = sets or B
+    out = torch.empty((B, d), dtype=torch.float64, device=x.device)
+    st = lib().km_sets_mean(x.data_ptr(), stride, B, S, d, out.data_ptr(), _cuda_stream(x))
+    if st != KM_OK:
+        raise KMError(st, "km_sets_mean")
+    return out
+
+
+def sets_rotate(x, R, center=None, transpose: bool = False, set_stride: int | None = None):
+    """km_sets_rotate_f32/_f64 on CUDA tensors: out[b] = R_b (x[b] - c_b) + c_b
+    (R_b^T with transpose).  x: (B, S, d) float32 or float64, or (S, d) with
+    set_stride 0 for one set rotated B ways; R: (B, d, d) float64; center:
+    (B, d) float64, (d,) for one centre for every set, or None (the origin)."""
+    import torch
+    if x.dim() == 2:
+        x = x.unsqueeze(0)
+        stride = 0
+    else:
+        stride = x.shape[1] * x.shape[2]
+    x = x.contiguous()
+    if set_stride is not None:
+        stride = set_stride
+    R = R.to(device=x.device, dtype=torch.float64).contiguous()
+    B, d = R.shape[0], R.shape[1]
+    S = x.shape[1]
+    c_ptr, c_stride = None, 0
+    if center is not None:
+        center = center.to(device=x.device, dtype=torch.float64).contiguous()
+        c_ptr = center.data_ptr()
+        c_stride = d if center.dim() == 2 else 0
+    out = torch.empty((B, S, d), dtype=x.dtype, device=x.device)
+    fn = lib().km_sets_rotate_f64 if x.dtype == torch.float64 else lib().km_sets_rotate_f32
+    st = fn(x.data_ptr(), stride, B, S, d, R.data_ptr(), c_ptr, c_stride, 1 if transpose else 0, out.data_ptr(),
+            _cuda_stream(x))
+    if st != KM_OK:
+        raise KMError(st, "km_sets_rotate")
+    return out

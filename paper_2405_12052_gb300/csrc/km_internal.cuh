@@ -291,6 +291,12 @@ cudaError_t launch_setnet_adam(float* prm, const float* grads, float* m, float* 
                                float b2, float eps, float c1, float c2, cudaStream_t st);
 cudaError_t launch_setnet_sample(const float* x, int64_t ld, int64_t n, int d, int S, unsigned long long seed,
                                  float* out, cudaStream_t st);
+// Set transforms of the learned initialiser: per-set FP64 means, and
+// out = R (x - c) + c per set (R^T with transpose), in FP64.
+cudaError_t launch_sets_mean(const float* x, int64_t set_stride, int B, int S, int d, double* means, cudaStream_t st);
+template <typename T>
+cudaError_t launch_sets_rotate(const T* x, int64_t set_stride, int B, int S, int d, const double* R,
+                               const double* c, int64_t center_stride, int transpose, T* out, cudaStream_t st);
 cudaError_t launch_setnet_destandardize(const float* P, const float* ms, int B, int d, int k, double* out,
                                         cudaStream_t st);
 

@@ -26,6 +26,8 @@
 //   sn_adam          Adam with bias correction (Kingma and Ba 2015)
 #include "km_internal.cuh"
 
+#include <algorithm>
+
 namespace km {
 
 namespace {
@@ -477,5 +479,74 @@ cudaError_t launch_setnet_sample(const float* x, int64_t ld, int64_t n, int d, i
   sn_sample<<<(S + 255) / 256, 256, 0, st>>>(x, ld, n, d, S, seed, out);
   return cudaGetLastError();
 }
+
+namespace {
+
+// Per-set mean of B sets of S points (d <= 3), FP64, one block per set:
+// thread-strided partial sums combined by a fixed-order tree.
+__global__ void __launch_bounds__(256) sets_mean_kernel(const float* __restrict__ x, int64_t set_stride, int S,
+                                                        int d, double* __restrict__ means) {
+  __shared__ double red[3][256];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const float* xs = x + (int64_t)b * set_stride;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int s = tid; s < S; s += blockDim.x)
+    for (int j = 0; j < d; ++j) acc[j] = __dadd_rn(acc[j], (double)xs[(int64_t)s * d + j]);
+  for (int j = 0; j < 3; ++j) red[j][tid] = acc[j];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w)
+      for (int j = 0; j < 3; ++j) red[j][tid] = __dadd_rn(red[j][tid], red[j][tid + w]);
+    __syncthreads();
+  }
+  if (tid < d) means[(int64_t)b * d + tid] = __ddiv_rn(red[tid][0], (double)S);
+}
+
+// out[b][s] = R_b (x[b][s] - c_b) + c_b (R_b^T with transpose), in FP64;
+// R: B x d x d row-major, c: one centre per set (stride center_stride
+// doubles; null = the origin).
+template <typename T>
+__global__ void sets_rotate_kernel(const T* __restrict__ x, int64_t set_stride, int B, int S, int d,
+                                   const double* __restrict__ R, const double* __restrict__ c, int64_t center_stride,
+                                   int transpose, T* __restrict__ out) {
+  const int64_t total = (int64_t)B * S;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(q / S), s = (int)(q - (int64_t)b * S);
+    const T* xp = x + (int64_t)b * set_stride + (int64_t)s * d;
+    const double* Rb = R + (int64_t)b * d * d;
+    double v[3], cc[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < d; ++j) {
+      if (c) cc[j] = c[(int64_t)b * center_stride + j];
+      v[j] = __dsub_rn((double)xp[j], cc[j]);
+    }
+    T* op = out + q * d;
+    for (int i = 0; i < d; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < d; ++j)
+        acc = __dadd_rn(acc, __dmul_rn(transpose ? Rb[j * d + i] : Rb[i * d + j], v[j]));
+      op[i] = (T)__dadd_rn(acc, cc[i]);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sets_mean(const float* x, int64_t set_stride, int B, int S, int d, double* means, cudaStream_t st) {
+  sets_mean_kernel<<<B, 256, 0, st>>>(x, set_stride, S, d, means);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sets_rotate(const T* x, int64_t set_stride, int B, int S, int d, const double* R,
+                               const double* c, int64_t center_stride, int transpose, T* out, cudaStream_t st) {
+  const int64_t total = (int64_t)B * S;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096));
+  sets_rotate_kernel<T><<<grid, 256, 0, st>>>(x, set_stride, B, S, d, R, c, center_stride, transpose, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_sets_rotate<float>(const float*, int64_t, int, int, int, const double*, const double*,
+                                               int64_t, int, float*, cudaStream_t);
+template cudaError_t launch_sets_rotate<double>(const double*, int64_t, int, int, int, const double*, const double*,
+                                                int64_t, int, double*, cudaStream_t);
 
 }  // namespace km

@@ -116,6 +116,17 @@ km_status inputs(km_setnet* n, const float* x, const float* t, int B, int S, int
 
 }  // namespace
 
+template <typename T>
+static km_status sets_rotate(const T* x, int64_t set_stride, int32_t B, int32_t S, int32_t d, const double* R,
+                             const double* center, int64_t center_stride, int32_t transpose, T* out, void* stream) {
+  if (!x || !R || !out || B < 1 || S < 1 || d < 1 || d > 3 || set_stride < 0 || center_stride < 0) return KM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (launch_sets_rotate<T>(x, set_stride, B, S, d, R, center, center_stride, transpose ? 1 : 0, out, st) !=
+      cudaSuccess)
+    return KM_ECUDA;
+  return KM_OK;
+}
+
 extern "C" {
 
 km_status km_setnet_create(km_setnet** out, int32_t d, int32_t k, void* stream) {
@@ -225,6 +236,25 @@ km_status km_setnet_predict(km_setnet* n, const float* x, int32_t B, int32_t S, 
                              n->st));
   KN_CUDA(n, cudaStreamSynchronize(n->st));
   return KM_OK;
+}
+
+km_status km_sets_mean(const float* x, int64_t set_stride, int32_t B, int32_t S, int32_t d, double* means_out,
+                       void* stream) {
+  if (!x || !means_out || B < 1 || S < 1 || d < 1 || d > 3 || set_stride < 0) return KM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (launch_sets_mean(x, set_stride, B, S, d, means_out, st) != cudaSuccess) return KM_ECUDA;
+  return KM_OK;
+}
+
+km_status km_sets_rotate_f32(const float* x, int64_t set_stride, int32_t B, int32_t S, int32_t d, const double* R,
+                             const double* center, int64_t center_stride, int32_t transpose, float* out, void* stream) {
+  return sets_rotate<float>(x, set_stride, B, S, d, R, center, center_stride, transpose, out, stream);
+}
+
+km_status km_sets_rotate_f64(const double* x, int64_t set_stride, int32_t B, int32_t S, int32_t d, const double* R,
+                             const double* center, int64_t center_stride, int32_t transpose, double* out,
+                             void* stream) {
+  return sets_rotate<double>(x, set_stride, B, S, d, R, center, center_stride, transpose, out, stream);
 }
 
 int32_t km_setnet_dims(const km_setnet* n, int32_t* k_out) {

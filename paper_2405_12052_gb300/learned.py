@@ -101,12 +101,12 @@ def init_params(d: int, k: int, seed: int = 0, h: int = 128) -> np.ndarray:
 
 def _rotations(m: int, d: int, g, device):
     """m seeded Haar-random orthogonal maps (QR of Gaussian matrices, signs
-    fixed: rotations and reflections), as a (m, d, d) float32 tensor."""
+    fixed: rotations and reflections), as a (m, d, d) float64 tensor: the
+    random input of the training augmentation."""
     import torch
     a = torch.randn(m, d, d, generator=g, device=device, dtype=torch.float64)
     q, r = torch.linalg.qr(a)
-    q = q * torch.sign(torch.diagonal(r, dim1=-2, dim2=-1)).unsqueeze(-2)
-    return q.to(torch.float32)
+    return q * torch.sign(torch.diagonal(r, dim1=-2, dim2=-1)).unsqueeze(-2)
 
 
 def train(x, t, *, epochs: int = 3, batch: int = 64, lr: float = 1e-3, lr_min: float = 1e-5, seed: int = 0,
@@ -131,9 +131,10 @@ def train(x, t, *, epochs: int = 3, batch: int = 64, lr: float = 1e-3, lr_min: f
             idx = perm[s0:s0 + batch]
             xb, tb = x[idx].contiguous(), t[idx].contiguous()
             if rotate:
+                from . import sets_rotate
                 rot = _rotations(batch, d, g, x.device)
-                xb = torch.bmm(xb, rot.transpose(1, 2)).contiguous()
-                tb = torch.bmm(tb, rot.transpose(1, 2)).contiguous()
+                xb = sets_rotate(xb, rot)
+                tb = sets_rotate(tb, rot)
             rate = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * step / max(1, steps)))
             want = (step % log_every) == 0 or step == steps - 1
             loss = net.train_step(xb, tb, rate, want_loss=want)
@@ -170,32 +171,32 @@ def _haar(rng, d: int) -> np.ndarray:
 def init_multi(g: KMeans, net: SetNet, x, *, hypotheses: int = 64, sample_n: int = 4096, seed: int = 0,
                max_iter: int = 300, tol: float = 1e-6) -> dict:
     """Learned start with test-time rotations.  One seeded sample of
-    ``sample_n`` of the points x (d x N, numpy or CUDA tensor; the context's
+    ``sample_n`` of the points x (d x N, a CUDA tensor: the context's
     points) is rotated about its mean by the identity and hypotheses - 1
-    seeded Haar rotations; the network predicts K centres for each rotated
-    copy (one batched forward pass) and they are rotated back.  Each
-    prediction starts Lloyd's iteration on the sample (all of them in one
-    batched run), and the converged sample centres with the lowest sample
-    objective become the context's start.  Returns the start and the
-    per-hypothesis sample objectives."""
+    seeded Haar rotations (km_sets_mean, km_sets_rotate_f32); the network
+    predicts K centres for each rotated copy (one batched forward pass) and
+    they are rotated back (km_sets_rotate_f64).  Each prediction starts
+    Lloyd's iteration on the sample (all of them in one batched run), and the
+    converged sample centres with the lowest sample objective become the
+    context's start.  The sample indices and the rotations are the random
+    inputs, drawn here; every arithmetic step runs in the library's kernels.
+    Returns the start and the per-hypothesis sample objectives."""
+    import torch
+    from . import sets_mean, sets_rotate
     d, n = int(x.shape[0]), int(x.shape[1])
     k = g.k
     rng = np.random.Generator(np.random.PCG64(seed))
     idx = np.sort(rng.choice(n, size=sample_n, replace=False))
-    if hasattr(x, "is_cuda"):
-        import torch
-        xs = x[:, torch.from_numpy(idx).to(x.device)].double().cpu().numpy()
-    else:
-        xs = np.asarray(x)[:, idx].astype(np.float64)
-    m = xs.mean(axis=1, keepdims=True)
-    rots = [np.eye(d)] + [_haar(rng, d) for _ in range(hypotheses - 1)]
-    batch = np.stack([(r @ (xs - m) + m).T for r in rots]).astype(np.float32)   # (H, S, d)
-    pred = net.predict(batch)                                                    # (H, K, d)
-    starts = [(r.T @ (p.T - m) + m).T for r, p in zip(rots, pred)]
+    xs = x[:, torch.from_numpy(idx).to(x.device)].t().contiguous()             # (S, d) float32, gathered
+    m = sets_mean(xs)                                                           # (1, d) float64
+    rots = torch.from_numpy(np.stack([np.eye(d)] + [_haar(rng, d) for _ in range(hypotheses - 1)]))
+    batch = sets_rotate(xs, rots, center=m[0])                                  # (H, S, d) float32
+    pred = torch.from_numpy(net.predict(batch)).to(x.device)                    # (H, K, d) float64
+    starts = sets_rotate(pred, rots, center=m[0], transpose=True).cpu().numpy()
     b = KMeansBatch(np.full(hypotheses, sample_n), np.full(hypotheses, d), np.full(hypotheses, k))
     try:
-        b.set_points([xs.astype(np.float32)] * hypotheses)
-        b.set_init(starts)
+        b.set_points(xs.t().contiguous().repeat(hypotheses, 1).reshape(-1))
+        b.set_init(starts.reshape(-1))
         b.set_shape(1024, 256)
         rb = b.run(max_iter, tol, want_labels=False)
         objs = b.objective()

@@ -96,3 +96,41 @@ def test_rotated_sample_start(km, oracle):
     assert kept <= rr["objective_kpp"] * (1 + 1e-6)
     print(json.dumps({k: v for k, v in rr.items() if k != "centroids"}))
     g.close()
+
+
+def test_learned_start_against_kmeanspp_on_held_out_mixtures(km):
+    """The measured gain and shortfall of the learned start (64 rotated
+    samples) against k-means++ + Lloyd on six held-out N = 1e6 anisotropic
+    mixtures (seeds 900..905, the bench's recipe at a tenth of its size),
+    tol 1e-6, at most 300 steps.  Recorded on GB300 when this test was
+    written: from the learned start Lloyd needs fewer full-data steps than
+    from k-means++ in 5 of 6 mixtures, and ends within 1e-6 of (or below) the
+    k-means++ objective in 3 of 6 (objective ratios 2.03, 1.08, 1.003, 0.65,
+    0.90, 0.92); the whole learned path (64 predictions, the batched sample
+    runs, the full run) takes longer than k-means++ + Lloyd.  Asserted: the
+    judged result never ends above the k-means++ objective (beyond 1e-6
+    relative), and the learned start needs fewer full-data steps in at least
+    4 of the 6; the objective ratios are printed."""
+    import torch
+    from paper_2405_12052_gb300 import learned
+    if not os.path.exists(learned.WEIGHTS):
+        pytest.skip("no committed weights")
+    net = learned.load()
+    n = 1_000_000
+    rows = []
+    for s in range(6):
+        x = synth.aniso_mixture(n, 3, 16, seed=900 + s)[0]
+        xt = torch.from_numpy(x).cuda()
+        g = km.KMeans(n, 3, 16)
+        g.set_points(xt, borrow=True)
+        u = np.random.default_rng(700 + s).random(16)
+        r = learned.run_with_fallback(g, net, u, seed=s, hypotheses=64, x=xt)
+        kept = r["objective_learned"] if r["used"] == "learned" else r["objective_kpp"]
+        assert kept <= r["objective_kpp"] * (1 + 1e-6)
+        rows.append({"seed": 900 + s, "iters_learned": r["iters_learned"], "iters_kpp": r["iters_kpp"],
+                     "objective_ratio": r["objective_learned"] / r["objective_kpp"], "used": r["used"]})
+        g.close()
+    fewer = sum(q["iters_learned"] < q["iters_kpp"] for q in rows)
+    within = sum(q["objective_ratio"] <= 1 + 1e-6 for q in rows)
+    print(json.dumps({"fewer_steps": fewer, "objective_within_1e-6_or_lower": within, "rows": rows}))
+    assert fewer >= 4, rows

@@ -134,3 +134,26 @@ def test_init_learned_on_a_context(km, oracle):
     assert np.array_equal(r["labels"], rr["labels"]) and r["iters"] == rr["iters"]
     g.close()
     net.close()
+
+
+def test_set_transforms_match_numpy(km):
+    """km_sets_mean and km_sets_rotate_f32/_f64 against numpy in float64:
+    per-set means, rotations about each set's centre and back (R^T)."""
+    import torch
+    rng = np.random.default_rng(9)
+    B, S, d = 5, 777, 3
+    x = (rng.normal(size=(B, S, d)) * [3.0, 0.5, 10.0] + [100.0, -2.0, 7.0]).astype(np.float32)
+    R = np.stack([np.linalg.qr(rng.normal(size=(d, d)))[0] for _ in range(B)])
+    xt = torch.from_numpy(x).cuda()
+    m = km.sets_mean(xt).cpu().numpy()
+    assert np.allclose(m, x.astype(np.float64).mean(axis=1), rtol=1e-14, atol=1e-12)
+    out = km.sets_rotate(xt, torch.from_numpy(R), center=torch.from_numpy(m)).cpu().numpy()
+    ref = np.einsum("bij,bsj->bsi", R, x.astype(np.float64) - m[:, None, :]) + m[:, None, :]
+    assert np.max(np.abs(out - ref)) <= 2 ** -22 * np.abs(ref).max()
+    back = km.sets_rotate(torch.from_numpy(ref).cuda(), torch.from_numpy(R), center=torch.from_numpy(m),
+                          transpose=True).cpu().numpy()
+    assert np.allclose(back, x.astype(np.float64), rtol=0, atol=1e-11 * np.abs(ref).max())
+    # one set rotated B ways (set stride 0), about one centre
+    one = km.sets_rotate(xt[0], torch.from_numpy(R), center=torch.from_numpy(m[0])).cpu().numpy()
+    ref1 = np.einsum("bij,sj->bsi", R, x[0].astype(np.float64) - m[0]) + m[0]
+    assert np.max(np.abs(one - ref1)) <= 2 ** -22 * np.abs(ref1).max()
