@@ -185,6 +185,7 @@ struct FastSmem {
   uint32_t* queue;          // [kWarps][kWarpQueue] flagged points
   uint32_t* win;            // [kWarps][nwin][k+1][WIN] 32-bit windows (per half-warp when nwin = 2); bin k discards
   int* cnt;                 // [2]: flagged, fp64-decided (block totals)
+  FastSmem() = default;
   __device__ FastSmem(unsigned char* sm, int kpad, int k, int nwin, int nbuf) {
     tab = reinterpret_cast<unsigned long long*>(sm);
     acc = reinterpret_cast<long long*>(tab + (size_t)kpad * DP);
@@ -562,8 +563,11 @@ __device__ __forceinline__ void process_tile(const FastArgs& a, FastSmem<D>& sm,
 #pragma unroll
           for (int qq = 0; qq < 4; ++qq) if (i0 + qq < a.n) a.labels8[i0 + qq] = (uint8_t)lab[4 * g + qq];
         }
-      } else if constexpr (FULL) {
+      } else if (FULL && !a.labels_unaligned) {
         *reinterpret_cast<int4*>(a.labels + i0) = make_int4(lab[4 * g], lab[4 * g + 1], lab[4 * g + 2], lab[4 * g + 3]);
+      } else if constexpr (FULL) {
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) a.labels[i0 + qq] = lab[4 * g + qq];
       } else {
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq) if (i0 + qq < a.n) a.labels[i0 + qq] = lab[4 * g + qq];
@@ -702,6 +706,177 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
   if (tid == 0) {
     if (sm.cnt[0]) atomicAdd(&a.ls->flagged, (unsigned long long)sm.cnt[0]);
     if (sm.cnt[1]) atomicAdd(&a.ls->fp64_decided, (unsigned long long)sm.cnt[1]);
+  }
+}
+
+// ---- Batched instances through the fused kernel's tile machinery ----
+//
+// Per tile (a run of one instance's points, a multiple of 256 long but the
+// instance's last), the block loads the instance's screen table, group table
+// and re-check centroids into shared memory; each warp then screens the
+// tile's 256-point warp-tiles w, w + 8, ... exactly as the fused kernel
+// does (same screen, flag test, re-check and exact sums), and the block
+// writes its int64 totals as the tile's partial row.  The regions of shared
+// memory have fixed bases (the layout of d = 3, K = 64), so instances of any
+// d follow one another without clearing: windows are zero after every flush.
+
+// Points of an instance are packed without padding, so the staging copies
+// are 4 bytes each (rows need not be 16-byte aligned); past N, zero-filled.
+template <int D>
+__device__ __forceinline__ void prefetch_tile_any(const FastArgs& a, float* xb, int64_t base, int lane) {
+#pragma unroll
+  for (int g = 0; g < kNG; ++g)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int off = g * kGS + 4 * lane + e;
+      const int64_t i = base + off;
+      const int bytes = i < a.n ? 4 : 0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const float* src = a.x + (int64_t)j * a.ld + (bytes ? i : 0);
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(xb + j * kWarpTile + off);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes));
+      }
+    }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+constexpr int kBatchWinWords = 2 * (kBatchMaxK + 1) * 7;  // per warp: two windows of 65 bins of 7 words
+
+template <int D>
+__device__ __forceinline__ FastSmem<D> batch_smem(unsigned char* raw) {
+  const FastSmem<3> f(raw, kBatchMaxK, kBatchMaxK, 2, 2);
+  FastSmem<D> s;
+  s.tab = f.tab;
+  s.acc = f.acc;
+  s.gtab = f.gtab;
+  s.ctil = f.ctil;
+  s.xbuf = f.xbuf;
+  s.queue = f.queue;
+  s.win = f.win;
+  s.cnt = f.cnt;
+  return s;
+}
+
+template <int D>
+__device__ void batch_fast_tile(const BatchArgs& ba, int t, const int4& tl, unsigned char* raw, int tid, int lane,
+                                int warp, int& nflag, int& n64) {
+  constexpr int DP = D + 1, WIN = 2 * D + 1, GS = FastSmem<D>::GS;
+  FastSmem<D> sm = batch_smem<D>(raw);
+  const int inst = tl.x;
+  const BatchInst bi = ba.inst[inst];
+  const int k = bi.k, kpad = bi.kpad;
+  const unsigned long long* tab2 = ba.tab2 + bi.tab_off;
+  for (int q = tid; q < kpad * DP; q += kThreads) {
+    const unsigned long long v = tab2[q];
+    sm.tab[q] = v;
+    const int c = q / DP, j = q - c * DP;
+    reinterpret_cast<float*>(sm.gtab + (size_t)(c >> 2) * GS + j)[c & 3] = __uint_as_float((uint32_t)v);
+  }
+  for (int q = tid; q < k; q += kThreads) sm.ctil[q] = ba.ctil4[bi.k_off + q];
+  __syncthreads();
+
+  FastArgs a{};
+  a.x = ba.x + bi.x_off; a.ld = bi.n; a.n = bi.n; a.k = k; a.kpad = kpad;
+  a.ctil = ba.ctil4 + bi.k_off; a.mu = ba.mu + bi.mu_off;
+  a.labels = ba.labels + bi.lab_off; a.labels8 = nullptr; a.store_labels = 1; a.nwin = 2;
+  a.labels_unaligned = (bi.lab_off & 3) != 0;
+  const IterConst ic = ba.ic[inst];
+  DataConst dc{};
+  for (int j = 0; j < kMaxDFast; ++j) dc.s[j] = j < 3 ? bi.s[j] : 0.f;
+  dc.A_max = bi.A_max; dc.G0 = bi.G0; dc.C_hi = bi.C_hi; dc.C_lo = bi.C_lo;
+  dc.bits_C_hi = bi.bits_C_hi; dc.bits_C_lo = bi.bits_C_lo;
+  float s[D];
+  unsigned long long s2[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) { s[j] = bi.s[j]; s2[j] = dup2(bi.s[j]); }
+  FastCtx cx;
+  cx.L = (uint32_t)ic.L; cx.mul = ic.mul; cx.kmask = ic.mul - 1u;
+  cx.ehi = __float_as_uint(ic.M) >> (32 - ic.L);
+  cx.M = ic.M;
+  {
+    const float ulp = __uint_as_float(__float_as_uint(ic.M) & 0x7f800000u) * 0x1p-23f;
+    cx.c0 = ic.thr_c0 * ulp;
+    cx.cA = (ic.thr_cA + ic.tau * ic.G) * ulp;
+  }
+  cx.tau = ic.tau;
+  cx.chi2 = dup2(dc.C_hi); cx.clo2 = dup2(dc.C_lo);
+  cx.k = k; cx.kpad = kpad;
+
+  uint32_t* wwarp = sm.win + (size_t)warp * kBatchWinWords;
+  uint32_t* wmine = wwarp + (size_t)(lane >> 4) * (k + 1) * WIN;
+  uint32_t* q = sm.queue + (size_t)warp * kWarpQueue;
+  float* xb = sm.xbuf + (size_t)warp * 2 * 3 * kWarpTile;
+  const int64_t first = tl.y;
+  const int nwt = (tl.z + kWarpTile - 1) / kWarpTile;  // warp-tiles of this tile
+  const int wid0 = (int)(first / kWarpTile) + warp;  // this warp's first warp-tile (index within the instance)
+  int qn = 0, m = 0, since_flush = 0;
+  if (warp < nwt) prefetch_tile_any<D>(a, xb, first + (int64_t)warp * kWarpTile, lane);
+  for (int wt = warp; wt < nwt; wt += kWarps, ++m) {
+    const int64_t base = first + (int64_t)wt * kWarpTile;
+    const float* xcur = xb + (m & 1) * D * kWarpTile;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (wt + kWarps < nwt)
+      prefetch_tile_any<D>(a, xb + ((m + 1) & 1) * D * kWarpTile, base + (int64_t)kWarps * kWarpTile, lane);
+    if (base + kWarpTile <= bi.n)
+      process_tile<D, 0, false, true>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
+    else
+      process_tile<D, 0, false, false>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
+    // 16 lanes x 8 points x 4 warp-tiles: <= 512 additions per bin
+    if (++since_flush == 4) {
+      flush_windows<D>(wwarp, sm.acc, k, 2, lane, dc.bits_C_hi, dc.bits_C_lo);
+      since_flush = 0;
+    }
+    if (qn > kWarpQueue - kWarpTile) {
+      __syncwarp();
+      drain_warp_queue<D>(a, sm, q, qn, wid0, kWarps, wwarp, wmine, sm.acc, lane, s, dc, ic.B_max, ic.tau, n64);
+      nflag += qn;
+      qn = 0;
+      since_flush = 0;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+  if (qn > 0) {
+    drain_warp_queue<D>(a, sm, q, qn, wid0, kWarps, wwarp, wmine, sm.acc, lane, s, dc, ic.B_max, ic.tau, n64);
+    nflag += qn;
+  } else if (warp < nwt) {
+    flush_windows<D>(wwarp, sm.acc, k, 2, lane, dc.bits_C_hi, dc.bits_C_lo);
+  }
+  __syncthreads();
+  // the tile's partial row; the totals go back to zero for the next tile
+  // (each thread its own entries; the next tile's flushes come after its
+  // first barrier)
+  long long* prow = ba.partials + ba.tile_poff[t];
+  for (int q2 = tid; q2 < k * DP; q2 += kThreads) {
+    prow[q2] = sm.acc[q2];
+    sm.acc[q2] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, KM_MINB) batch_fast_kernel(BatchArgs ba) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const FastSmem<3> base(smraw, kBatchMaxK, kBatchMaxK, 2, 2);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int q = tid; q < kWarps * kBatchWinWords; q += kThreads) base.win[q] = 0u;
+  for (int q = tid; q < kBatchMaxK * 4; q += kThreads) base.acc[q] = 0;
+  if (tid < 2) base.cnt[tid] = 0;
+  __syncthreads();
+  int nflag = 0, n64 = 0;
+  for (int t = blockIdx.x; t < ba.ntiles; t += gridDim.x) {
+    const int4 tl = ba.tiles[t];
+    if (ba.state[tl.x].done) continue;  // block-uniform
+    const int d = ba.inst[tl.x].d;
+    if (d == 3) batch_fast_tile<3>(ba, t, tl, smraw, tid, lane, warp, nflag, n64);
+    else if (d == 2) batch_fast_tile<2>(ba, t, tl, smraw, tid, lane, warp, nflag, n64);
+    else batch_fast_tile<1>(ba, t, tl, smraw, tid, lane, warp, nflag, n64);
+  }
+  if (lane == 0 && nflag) atomicAdd(&base.cnt[0], nflag);
+  if (n64) atomicAdd(&base.cnt[1], n64);
+  __syncthreads();
+  if (tid == 0) {
+    if (base.cnt[0]) atomicAdd(ba.flagged, (unsigned long long)base.cnt[0]);
+    if (base.cnt[1]) atomicAdd(ba.fp64, (unsigned long long)base.cnt[1]);
   }
 }
 
@@ -861,6 +1036,24 @@ cudaError_t launch_assign_fast(int d, int grid, size_t smem, cudaStream_t st, co
     case 4: return launch_fast_d<4>(grid, smem, st, a);
     default: return cudaErrorInvalidValue;
   }
+}
+
+static size_t batch_fast_smem() { return fast_smem_bytes(3, kBatchMaxK, kBatchMaxK, 2); }
+
+cudaError_t launch_batch_fast(const BatchArgs& a, int grid, cudaStream_t st) {
+  const size_t smem = batch_fast_smem();
+  cudaError_t e = cudaFuncSetAttribute(batch_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  batch_fast_kernel<<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+int batch_fast_blocks_per_sm() {
+  const size_t smem = batch_fast_smem();
+  int nb = 0;
+  cudaFuncSetAttribute(batch_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_fast_kernel, kThreads, smem) != cudaSuccess) return 1;
+  return nb > 0 ? nb : 1;
 }
 
 size_t generic_smem_bytes(int, int) { return 0; }

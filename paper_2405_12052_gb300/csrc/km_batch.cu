@@ -23,6 +23,7 @@
 // Stopped instances are skipped by both kernels, so a captured run of U
 // steps can be replayed until no instance is active.
 #include "km_internal.cuh"
+#include "km_tables.cuh"
 
 #include <algorithm>
 
@@ -345,6 +346,10 @@ __global__ void __launch_bounds__(256) batch_update_kernel(BatchArgs a) {
     if (tid < w) s_bmax[tid] = fmax(s_bmax[tid], s_bmax[tid + w]);
     __syncthreads();
   }
+  // the fused kernel's screen tables of the new centres
+  __shared__ double s_fB[kBatchMaxK];
+  fast_screen_tables(mu, bi.s, bi.A_max, k, d, bi.kpad, a.tie_rel, a.ctil4 + bi.k_off, a.ic + inst,
+                     a.tab2 + bi.tab_off, s_fB);
   if (tid == 0) {
     const double E2 = s_red[0], E = sqrt(E2);
     st->E2 = E2;
@@ -384,6 +389,9 @@ __global__ void __launch_bounds__(256) batch_tables_kernel(BatchArgs a) {
     __syncthreads();
   }
   if (tid == 0) a.state[inst].B_max = (float)(s_bmax[0] * (1.0 + 1e-6));
+  __shared__ double s_fB[kBatchMaxK];
+  fast_screen_tables(a.mu + bi.mu_off, bi.s, bi.A_max, k, d, bi.kpad, a.tie_rel, a.ctil4 + bi.k_off, a.ic + inst,
+                     a.tab2 + bi.tab_off, s_fB);
 }
 
 // Per instance (one block): coordinate ranges, non-finite values, the shift

@@ -36,6 +36,11 @@ struct km_batch {
   int64_t* tile_poff = nullptr;
   long long* partials = nullptr;
   unsigned long long* stats = nullptr;  // [0] flagged, [1] fp64, [2] non-finite
+  unsigned long long* tab2 = nullptr;   // fused kernel: per-instance screen tables
+  float4* ctil4 = nullptr;
+  IterConst* ic = nullptr;
+  int64_t total_tab = 0;
+  int kind = 0;                         // assign kernel: 0 the batch kernel, 1 the fused kernel's tiles
   int* active = nullptr;
   int64_t max_tiles = 0, max_partials = 0;
   // launch shape
@@ -52,6 +57,8 @@ namespace {
 
 constexpr int kTileCand[2] = {512, 1024};
 constexpr int kThreadCand[3] = {128, 256, 512};
+// the fused kernel's tiles (a multiple of its 256-point warp-tiles; 256 threads)
+constexpr int kFastTileCand[2] = {2048, 8192};
 constexpr int kGraphSteps = 4;
 
 km_status bfail(km_batch* b, km_status s, const std::string& m) {
@@ -78,6 +85,7 @@ BatchArgs bargs(km_batch* b) {
   a.ntiles = b->ntiles; a.partials = b->partials; a.labels = b->labels; a.mu = b->mu; a.ctil = b->ctil;
   a.counts = b->counts; a.flagged = b->stats; a.fp64 = b->stats + 1; a.active = b->active;
   a.tau = (float)(b->opt.tie_rel * (1.0 + 1e-4)); a.e_mode = b->opt.e_mode; a.tol = 0.0;
+  a.tab2 = b->tab2; a.ctil4 = b->ctil4; a.ic = b->ic; a.tie_rel = b->opt.tie_rel;
   return a;
 }
 
@@ -121,8 +129,13 @@ void drop_graph(km_batch* b) {
 }
 
 int grid_for(km_batch* b, int threads) {
-  const int64_t g = std::min<int64_t>(b->ntiles, (int64_t)b->sms * batch_blocks_per_sm(threads));
+  const int per_sm = b->kind == 1 ? batch_fast_blocks_per_sm() : batch_blocks_per_sm(threads);
+  const int64_t g = std::min<int64_t>(b->ntiles, (int64_t)b->sms * per_sm);
   return (int)std::max<int64_t>(1, g);
+}
+
+cudaError_t launch_assign_kind(km_batch* b, const BatchArgs& a) {
+  return b->kind == 1 ? launch_batch_fast(a, b->grid, b->st) : launch_batch_assign(a, b->grid, b->threads, b->st);
 }
 
 }  // namespace
@@ -151,6 +164,9 @@ km_status km_batch_create(km_batch** out, int32_t count, const int64_t* n, const
     std::memset(&bi, 0, sizeof(bi));
     bi.n = n[i]; bi.d = d[i]; bi.k = k[i];
     bi.x_off = xo; bi.lab_off = lo; bi.mu_off = (int32_t)mo; bi.k_off = (int32_t)ko;
+    bi.kpad = (k[i] + 7) / 8 * 8;
+    bi.tab_off = (int32_t)b->total_tab;
+    b->total_tab += (int64_t)bi.kpad * (d[i] + 1);
     xo += n[i] * d[i]; lo += n[i]; mo += (int64_t)k[i] * d[i]; ko += k[i];
     const int64_t nt = (n[i] + kTileCand[0] - 1) / kTileCand[0];
     tiles_max += nt;
@@ -178,6 +194,9 @@ km_status km_batch_create(km_batch** out, int32_t count, const int64_t* n, const
   KB_CUDA(b, balloc(&b->tile_poff, (size_t)tiles_max));
   KB_CUDA(b, balloc(&b->partials, (size_t)part_max));
   KB_CUDA(b, balloc(&b->stats, 3));
+  KB_CUDA(b, balloc(&b->tab2, (size_t)b->total_tab));
+  KB_CUDA(b, balloc(&b->ctil4, (size_t)ko));
+  KB_CUDA(b, balloc(&b->ic, (size_t)count));
   KB_CUDA(b, balloc(&b->active, 1));
   KB_CUDA(b, cudaMemcpyAsync(b->inst, b->hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, b->st));
   KB_CUDA(b, cudaMemsetAsync(b->state, 0, sizeof(BatchState) * count, b->st));
@@ -235,31 +254,43 @@ km_status km_batch_tune(km_batch* b, int32_t* tile_out, int32_t* threads_out) {
   KB_CUDA(b, cudaEventCreate(&e0));
   KB_CUDA(b, cudaEventCreate(&e1));
   float best = 3.0e38f;
-  int bt = kTileCand[1], bth = 256;
+  int bt = kTileCand[1], bth = 256, bkind = 0;
   b->tune_ms.clear();
   // the assign kernel writes labels, partials and counters only: timing it
-  // leaves the centroids and the loop state untouched
-  for (int tp : kTileCand) {
+  // leaves the centroids and the loop state untouched.  Candidates: the
+  // batch kernel's tiles x block sizes, then the fused kernel's tiles.
+  auto time_shape = [&](int kind, int tp, int th) -> km_status {
     km_status s = build_tiles(b, tp);
     if (s != KM_OK) return s;
+    b->kind = kind;
+    b->threads = th;
+    b->grid = grid_for(b, th);
+    BatchArgs a = bargs(b);
+    KB_CUDA(b, launch_assign_kind(b, a));  // warm-up
+    KB_CUDA(b, cudaEventRecord(e0, b->st));
+    for (int r = 0; r < 3; ++r) KB_CUDA(b, launch_assign_kind(b, a));
+    KB_CUDA(b, cudaEventRecord(e1, b->st));
+    KB_CUDA(b, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    KB_CUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+    b->tune_ms.push_back(ms / 3.f);
+    if (ms < best) { best = ms; bt = tp; bth = th; bkind = kind; }
+    return KM_OK;
+  };
+  for (int tp : kTileCand)
     for (int th : kThreadCand) {
-      BatchArgs a = bargs(b);
-      const int g = grid_for(b, th);
-      KB_CUDA(b, launch_batch_assign(a, g, th, b->st));  // warm-up
-      KB_CUDA(b, cudaEventRecord(e0, b->st));
-      for (int r = 0; r < 3; ++r) KB_CUDA(b, launch_batch_assign(a, g, th, b->st));
-      KB_CUDA(b, cudaEventRecord(e1, b->st));
-      KB_CUDA(b, cudaEventSynchronize(e1));
-      float ms = 0.f;
-      KB_CUDA(b, cudaEventElapsedTime(&ms, e0, e1));
-      b->tune_ms.push_back(ms / 3.f);
-      if (ms < best) { best = ms; bt = tp; bth = th; }
+      km_status s = time_shape(0, tp, th);
+      if (s != KM_OK) return s;
     }
+  for (int tp : kFastTileCand) {
+    km_status s = time_shape(1, tp, 256);
+    if (s != KM_OK) return s;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   km_status s = build_tiles(b, bt);
   if (s != KM_OK) return s;
+  b->kind = bkind;
   b->threads = bth;
   b->grid = grid_for(b, bth);
   KB_CUDA(b, cudaMemsetAsync(b->stats, 0, sizeof(unsigned long long) * 2, b->st));
@@ -274,12 +305,14 @@ km_status km_batch_tune(km_batch* b, int32_t* tile_out, int32_t* threads_out) {
 km_status km_batch_set_shape(km_batch* b, int32_t tile_points, int32_t threads) {
   if (!b) return KM_EINVAL;
   if (!b->have_points) return bfail(b, KM_ESTATE, "set_points first");
-  bool ok_t = false, ok_th = false;
+  bool ok_t = false, ok_th = false, fast = false;
   for (int tp : kTileCand) ok_t = ok_t || tp == tile_points;
   for (int th : kThreadCand) ok_th = ok_th || th == threads;
-  if (!ok_t || !ok_th) return bfail(b, KM_EINVAL, "tile_points or threads is not one the tuner times");
+  for (int tp : kFastTileCand) fast = fast || (tp == tile_points && threads == 256);
+  if (!fast && (!ok_t || !ok_th)) return bfail(b, KM_EINVAL, "tile_points or threads is not one the tuner times");
   km_status s = build_tiles(b, tile_points);
   if (s != KM_OK) return s;
+  b->kind = fast ? 1 : 0;
   b->threads = threads;
   b->grid = grid_for(b, threads);
   b->tune_ms.clear();
@@ -318,7 +351,7 @@ km_status km_batch_run(km_batch* b, int32_t max_iter, double tol, int32_t* label
     cudaGraph_t g = nullptr;
     KB_CUDA(b, cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
     for (int r = 0; r < kGraphSteps; ++r) {
-      launch_batch_assign(a, b->grid, b->threads, b->st);
+      launch_assign_kind(b, a);
       launch_batch_update(a, b->count, b->st);
     }
     cudaError_t ce = cudaStreamEndCapture(b->st, &g);
@@ -335,7 +368,7 @@ km_status km_batch_run(km_batch* b, int32_t max_iter, double tol, int32_t* label
       KB_CUDA(b, cudaGraphLaunch(b->graph, b->st));
       done_steps += b->graph_steps;
     } else {
-      KB_CUDA(b, launch_batch_assign(a, b->grid, b->threads, b->st));
+      KB_CUDA(b, launch_assign_kind(b, a));
       KB_CUDA(b, launch_batch_update(a, b->count, b->st));
       done_steps += 1;
     }
@@ -404,7 +437,7 @@ void km_batch_destroy(km_batch* b) {
   if (!b) return;
   drop_graph(b);
   void* bufs[] = {b->x, b->labels, b->mu, b->ctil, b->counts, b->inst, b->state, b->tiles,
-                  b->tile_poff, b->partials, b->stats, b->active};
+                  b->tile_poff, b->partials, b->stats, b->active, b->tab2, b->ctil4, b->ic};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (b->own_stream && b->st) cudaStreamDestroy(b->st);

@@ -117,6 +117,7 @@ struct FastArgs {
   uint8_t* labels8;                // non-null: labels are written here as bytes (K <= 256), not to labels
   int ignore_done;                 // 1: run even after the stop flag (the final labels pass)
   int const_tab;                   // 1: the screen reads the table from the constant bank (copied at launch)
+  int labels_unaligned;            // 1: labels + i may not be 16-byte aligned (store them one by one)
 };
 
 struct GenericArgs {
@@ -222,6 +223,7 @@ struct BatchInst {        // per instance, written at set_points (scan kernel) a
   int64_t n, x_off, lab_off;       // points; element offset of row 0 (rows of n); label offset
   int32_t d, k, mu_off, k_off;     // mu/ctil offset (K*d), counts offset (K)
   int32_t tile0, ntiles;           // the instance's tiles (contiguous in the tile list)
+  int32_t kpad, tab_off;           // fused-kernel screen table: kpad = K rounded up to 8, offset in tab2
   float s[3];                      // shift (FP32 midrange)
   float A_max;                     // max fl32 ||x - s||^2
   int32_t G0;                      // fixed-point grid exponent
@@ -254,11 +256,20 @@ struct BatchArgs {
   float tau;
   int e_mode;
   double tol;
+  // the fused kernel's per-instance screen tables (written by the update)
+  unsigned long long* tab2;       // [sum kpad_i (d_i + 1)] packed pairs
+  float4* ctil4;                  // [sum K_i] fl32(mu - s)
+  IterConst* ic;                  // [count] screen constants
+  double tie_rel;
 };
 
 cudaError_t launch_batch_scan(const float* x, BatchInst* inst, int count, unsigned long long* bad, cudaStream_t st);
 cudaError_t launch_batch_tables(const BatchArgs& a, int count, cudaStream_t st);
 cudaError_t launch_batch_assign(const BatchArgs& a, int grid, int threads, cudaStream_t st);
+// The batch through the fused kernel's tile machinery (256 threads per block;
+// tiles of a multiple of 256 points).
+cudaError_t launch_batch_fast(const BatchArgs& a, int grid, cudaStream_t st);
+int batch_fast_blocks_per_sm();
 cudaError_t launch_batch_update(const BatchArgs& a, int count, cudaStream_t st);
 int batch_blocks_per_sm(int threads);
 cudaError_t launch_batch_objective(const float* x, const BatchInst* inst, const int32_t* labels, const double* mu,

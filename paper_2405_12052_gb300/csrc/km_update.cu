@@ -9,6 +9,7 @@
 // mu_k = S_k / n_k (an empty cluster keeps mu_k), forms E^2 with a fixed-order
 // tree, tests the stop rule, and writes the next step's screen tables.
 #include "km_internal.cuh"
+#include "km_tables.cuh"
 
 namespace km {
 
@@ -52,91 +53,15 @@ __device__ __forceinline__ uint32_t ordered(float f) {
   return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
-// Screen tables for the next step from mu (one block).  Fused path: c~ and
-// ||c~||^2, the bias M, the scale sigma and the flag constants; generic
-// path: c~ and B_max only.
+// Screen tables for the next step from mu (one block).  Fused path: the
+// tables of fast_screen_tables (km_tables.cuh); generic path: c~ and B_max
+// only.
 __device__ void prepare_tables(const UpdateArgs& a, double* sB) {
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nth = blockDim.x * blockDim.y;
   const int k = a.k, d = a.d;
-  __shared__ int sh_sigma;
-  __shared__ double sh_M, sh_dummy;
   if (a.fast) {
-    const DataConst* dc = a.dc;
-    for (int c = tid; c < k; c += nth) {
-      float cv[4] = {0.f, 0.f, 0.f, 0.f};
-      double B = 0.0;
-      for (int j = 0; j < d; ++j) {
-        cv[j] = __double2float_rn(__dsub_rn(a.mu[(size_t)c * d + j], (double)dc->s[j]));
-        B = __dadd_rn(B, __dmul_rn((double)cv[j], (double)cv[j]));
-      }
-      a.ctil4[c] = make_float4(cv[0], cv[1], cv[2], cv[3]);
-      sB[c] = B;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double bmax = 0.0;
-      for (int c = 0; c < k; ++c) bmax = fmax(bmax, sB[c]);
-      const int kpad = a.kpad;
-      int L = 1;
-      while ((1 << L) < kpad) ++L;
-      int E;
-      double frac, hw;
-      if (L <= 6) {
-        const int base = 1 << (7 - L), step = 1 << (9 - L);
-        E = base + ((127 - base) / step) * step;
-        frac = 1.5; hw = 0.5;
-      } else if (L == 7) {
-        E = 125; frac = 1.25; hw = 0.25;
-      } else {
-        E = 126; frac = 1.375; hw = 0.125;
-      }
-      const int eM = E - 127;
-      const double M = ldexp(frac, eM);
-      const double top = ldexp(hw, eM);
-      const double P = (dc->A_max * (1.0 + 0x1p-20) + 2.0 * bmax) * (1.0 + 0x1p-10) + 1e-300;
-      int sigma = ilogb(top / P);
-      if (ldexp(P, sigma) >= top) sigma -= 1;
-      sigma = max(-120, min(120, sigma));
-      const double G = ldexp(1.0, sigma - eM + 23);
-      const double u = 0x1p-24, u64x = 4.1 * 0x1p-53;
-      IterConst ic;
-      ic.M = (float)M;
-      ic.L = L;
-      ic.mul = 1u << L;
-      ic.bitsM_low = __float_as_uint(ic.M) & ((1u << (32 - L)) - 1u);
-      ic.G = (float)G;
-      ic.thr_c0 = __double2float_ru(((double)(d + 1) + 2.0 + (8.002 * u + u64x * (d + 1)) * bmax * G) *
-                                    (1.0 + 1e-4));
-      ic.thr_cA = __double2float_ru((4.001 * u + u64x * (d + 1)) * G * (1.0 + 1e-4) * (1.0 + 1e-5));
-      ic.tau = __double2float_ru(a.tie_rel * (1.0 + 1e-4));
-      ic.B_max = __double2float_ru(bmax);
-      ic.pad[0] = ic.pad[1] = ic.pad[2] = 0.f;
-      *a.ic = ic;
-      sh_sigma = sigma;
-      sh_M = M;
-      sh_dummy = (L <= 6 ? ldexp(2.0 - 0x1p-23, eM) : ldexp(1.5 - 0x1p-23, eM));
-    }
-    __syncthreads();
-    const int sigma = sh_sigma, dp = d + 1;
-    const float scale = -ldexpf(1.0f, sigma + 1);
-    for (int c = tid; c < a.kpad; c += nth) {
-      unsigned long long* row = a.tab2 + (size_t)c * dp;
-      if (c < k) {
-        const float4 cv4 = a.ctil4[c];
-        const float cv[4] = {cv4.x, cv4.y, cv4.z, cv4.w};
-        for (int j = 0; j < d; ++j) {
-          const uint32_t b = __float_as_uint(__fmul_rn(cv[j], scale));
-          row[j] = ((unsigned long long)b << 32) | b;
-        }
-        const uint32_t nb = __float_as_uint(__double2float_rn(sh_M + ldexp(sB[c], sigma)));
-        row[d] = ((unsigned long long)nb << 32) | nb;
-      } else {
-        for (int j = 0; j < d; ++j) row[j] = 0ull;
-        const uint32_t nb = __float_as_uint((float)sh_dummy);
-        row[d] = ((unsigned long long)nb << 32) | nb;
-      }
-    }
+    fast_screen_tables(a.mu, a.dc->s, a.dc->A_max, k, d, a.kpad, a.tie_rel, a.ctil4, a.ic, a.tab2, sB);
   } else {
     __shared__ unsigned int sh_bmax_bits;
     if (tid == 0) sh_bmax_bits = 0u;

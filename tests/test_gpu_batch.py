@@ -47,7 +47,26 @@ def test_batch_matches_oracle_per_instance(km, oracle):
     r = b.run(100, 1e-6)
     _check_against_oracle(b, insts, r, oracle, 100, 1e-6)
     info = b.info()
-    assert info["tuned"] == 1 and info["tile_points"] in (512, 1024) and info["tune_candidates"] == 6
+    assert info["tuned"] == 1 and info["tile_points"] in (512, 1024, 2048, 8192) and info["tune_candidates"] == 8
+    b.close()
+
+
+@pytest.mark.parametrize("shape", [(512, 128), (1024, 512), (2048, 256), (8192, 256)])
+def test_batch_every_shape_matches_oracle(km, oracle, shape):
+    """Every launch shape the tuner times gives the oracle's results: the
+    batch kernel's tiles, and the fused kernel's tile machinery (tiles of
+    2048 and 8192 points: instances of d = 1, 2 and 3 following one another
+    in a block, partial tiles, rows not 16-byte aligned in the packed
+    layout, labels at odd offsets)."""
+    insts = synth.batch_instances(40, seed=15, n_lo=300, n_hi=30_000)
+    x1 = np.linspace(-3, 3, 1001, dtype=np.float32)[None, :]
+    insts.insert(3, dict(x=x1, mu0=np.array([[-1.0], [0.5], [2.0]]), n=1001, d=1, k=3))
+    b = _batch(km, insts)
+    b.set_shape(*shape)
+    r = b.run(60, 1e-6)
+    _check_against_oracle(b, insts, r, oracle, 60, 1e-6)
+    info = b.info()
+    assert (info["tile_points"], info["threads"]) == shape
     b.close()
 
 
@@ -99,7 +118,7 @@ def test_tuner_cache_reuses_the_shape(km, oracle, tmp_path):
     cache = str(tmp_path / "tune.json")
     b1 = _batch(km, insts)
     shape1 = b1.tune(cache=cache)
-    assert len(b1.info()["tune_ms"]) == 6
+    assert len(b1.info()["tune_ms"]) == 8
     r1 = b1.run(100, 1e-6)
     b1.close()
     b2 = _batch(km, insts)
