@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--batch-ttc", type=int, default=256,
                     help="default line: instances of the batch recipe (the first ones) run to convergence "
                          "batched and one after another (0: skip)")
+    ap.add_argument("--no-extra", dest="extra", action="store_false",
+                    help="default line: skip the precision workloads' and the k-means++ seeding's records")
     ap.add_argument("--plain-every", type=int, default=1,
                     help="batch workloads: time plain km_run on every m-th instance (scaled up)")
     return ap.parse_args()
@@ -459,6 +461,12 @@ def run_ours(args, ws, rank, local):
            "time_to_converge": ttc}
     if args.ttc and args.batch_ttc > 0 and ws == 1:
         out["batch_time_to_converge"] = batch_ttc(args.batch_ttc, dev)
+    if args.extra and ws == 1 and args.workload == "plain_3d_n1e8_k32" and not args.n:
+        # the other configurations' per-step numbers and the GPU k-means++
+        # seeding of these points, measured in the same run
+        out["other_workloads"] = [extra_workload(km, name, dev, stream) for name in
+                                  ("precision_offset_3d_n2p27_k256", "precision_highd_64d_n1e7_k1024")]
+        out["kmeanspp_seeding"] = kmeanspp_record(km, xt, k, dev)
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     if rank == 0:
@@ -483,6 +491,87 @@ def gen_batch(count, seed=0):
     jobs = [(i, int(ns[i]), int(ds[i]), int(ks[i])) for i in range(count)]
     with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
         return pool.map(_gen_instance, jobs, chunksize=8)
+
+
+def extra_workload(km, name, dev, stream, steps=10, warmup=3):
+    """Per-step numbers of another configuration (points resident, the
+    library's default path for its shape): assign time by CUDA events around
+    each launch, the step time, evaluations/s and the roofline fraction of the
+    assign launches."""
+    import torch
+    w = load_workload(name, 0)
+    x, mu0, k = w["x"], w["mu0"], w["k"]
+    d, n = x.shape
+    xt = torch.from_numpy(x).to(dev)
+    g = km.KMeans(n, d, k, stream=stream, label_bytes=1 if (k <= 256 and d != 64) else 4)
+    g.set_points(xt, borrow=True)
+    g.set_init(mu0)
+    g.begin(warmup + steps, -1.0)
+    for _ in range(warmup):
+        g.assign_async()
+        g.update_async()
+    torch.cuda.synchronize(dev)
+    ea = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    eb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for i in range(steps):
+        ea[i].record(stream)
+        g.assign_async()
+        eb[i].record(stream)
+        g.update_async()
+    s1.record(stream)
+    s1.synchronize()
+    st = g.stats()
+    g.close()
+    del xt
+    assign_ms = statistics.mean(ea[i].elapsed_time(eb[i]) for i in range(steps))
+    step_ms = s0.elapsed_time(s1) / steps
+    pk, src = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if st["path"] == 3:
+        ach = 2.0 * n * k * d / (assign_ms / 1e3) / 1e12
+        peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0)))
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": f"bf16 dense, sustained, {src} peaks; 2*N*K*d flops per launch"}
+    else:
+        peak = sms * FP32_LANES_PER_SM * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        ach = 3.0 * n * k * d / (assign_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": "SMs x 128 FP32 lanes x 2 flops x sm_max_mhz; 3*N*K*d flops per launch"}
+    return {"workload": name, "n": n, "d": d, "k": k, "steps": steps, "warmup": warmup,
+            "assign_ms": assign_ms, "ms_per_step": step_ms, "evals_per_s": n * k / (step_ms / 1e3),
+            "flagged_per_step": st["flagged"], "fp64_decided_per_step": st["fp64_decided"],
+            "path": {1: "fused FFMA2", 2: "generic", 3: "tcgen05 BF16 GEMM-form"}.get(st["path"]),
+            "roofline": roof}
+
+
+def kmeanspp_record(km, xt, k, dev, reps=3):
+    """GPU k-means++ seeding (K rounds of D^2 sampling) on the resident points:
+    median wall time of `reps` seedings after one warm-up."""
+    import numpy as np
+    import torch
+    d, n = int(xt.shape[0]), int(xt.shape[1])
+    g = km.KMeans(n, d, k)
+    g.set_points(xt, borrow=True)
+    g.init_kmeanspp(np.random.default_rng(99).random(k))
+    times = []
+    for r in range(reps):
+        u = np.random.default_rng(100 + r).random(k)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g.init_kmeanspp(u)
+        torch.cuda.synchronize(dev)
+        times.append(time.perf_counter() - t0)
+    g.close()
+    t = statistics.median(times)
+    mhz = float(peaks()[0].get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = FP64_ADDMUL_PER_SM_CYCLE * sms * mhz * 1e6 / 1e12
+    ach = 3.0 * d * n * k / t / 1e12
+    return {"n": n, "d": d, "k": k, "ms_per_seeding": 1e3 * t, "evals_per_s": n * k / t,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak_ops, "unit": "Tops/s (FP64 add/mul)",
+                         "frac": ach / peak_ops}}
 
 
 def batch_ttc(count, dev):
