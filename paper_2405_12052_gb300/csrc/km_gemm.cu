@@ -523,8 +523,15 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
           const uint32_t c0 = __vcmpleu2(w.x, qt | (qt << 16)), c1 = __vcmpleu2(w.y, qt | (qt << 16));
           return (c0 & 1u) | ((c0 >> 15) & 2u) | ((c1 & 1u) << 2) | ((c1 >> 13) & 8u);
         };
+        // this thread's 4-bit masks of the point's slots, kept for the
+        // candidate pass below (kSlots x 4 bits fit in 64)
+        unsigned long long masks = 0ull;
         int mine = 0;
-        for (int j = 0; j < ns; ++j) mine += __popc(slot_mask(j));
+        for (int j = 0; j < ns; ++j) {
+          const uint32_t mm = slot_mask(j);
+          masks |= (unsigned long long)mm << (4 * j);
+          mine += __popc(mm);
+        }
         const int n1 = __shfl_xor_sync(0xffffffffu, mine, 1);  // sub ^ 1
         const int n2 = __shfl_xor_sync(0xffffffffu, mine, 2);  // sub ^ 2
         const int n3 = __shfl_xor_sync(0xffffffffu, n1, 2);    // sub ^ 3
@@ -553,7 +560,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
           unsigned short* cl = reinterpret_cast<unsigned short*>(a.tie_list + 3 * (size_t)entry) + 4 + before;
           int q = 0;
           for (int j = 0; j < ns; ++j) {
-            uint32_t mm = slot_mask(j);
+            uint32_t mm = (uint32_t)(masks >> (4 * j)) & 0xFu;
             while (mm) {
               const int bb = __ffs((int)mm) - 1;
               mm &= mm - 1u;
@@ -575,11 +582,11 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
         // tile (written again only after its first-group barrier)
         __syncwarp();
         if (lead) {
+          // (the slots' minima need no clearing: only slots below the next
+          // tile's count are read, and each of those is written first)
           es.cnt[pp] = 0;
           es.over[pp] = 0;
           es.thr[par * kGM + pp] = 0x7f800000u;  // next used by tile l + 2
-#pragma unroll
-          for (int j = 0; j < kSlots; ++j) es.smin[pp * kSlots + j] = 0u;
         }
       }
       // the next tile's start threshold; the barrier publishes it and keeps
