@@ -420,7 +420,7 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
     KM_CUDA(c, dalloc(&c->nprime, (size_t)c->kpad));
     KM_CUDA(c, dalloc(&c->gc, 1));
     KM_CUDA(c, dalloc(&c->rescue_list, (size_t)n));
-    KM_CUDA(c, dalloc(&c->tie_list, (size_t)n * 3));
+    KM_CUDA(c, dalloc(&c->tie_list, (size_t)gemm_tie_entries(n, c->G) * 3));
     KM_CUDA(c, dalloc(&c->rescue_count, 2));
     c->ms_max_chunks = (int)msort_max_chunks(n, k);
     KM_CUDA(c, dalloc(&c->ms_counts, (size_t)k));

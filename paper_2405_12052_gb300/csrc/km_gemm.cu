@@ -15,7 +15,7 @@
 //    binade [1, 2): r = M + 2^sigma (h - 2 S)) and the minimum of each half
 //    of 16 columns.  A half whose minimum is within the point's threshold is
 //    stored whole to shared memory (up to kSlots halves per point, 16 bits
-//    per value relative to the half's minimum).  The threshold is the
+//    per value: bits 8..23 of its FP32 pattern).  The threshold is the
 //    best r seen so far plus the candidate window Delta(x), which bounds every
 //    operand and FP32 rounding of the screen plus the oracle's FP64 error and
 //    1e-5 D, so the kept set always holds the exact argmin and all near ties.
@@ -52,12 +52,12 @@ constexpr int kHalf = 16;         // values per stored half
 constexpr int kPtStride = kSlots * kHalf * 2 + 16;  // bytes per point (padding spreads banks)
 constexpr int kTileBytes = kGM * kGemmD * 2;   // 16 KB of 16-bit operands per point tile
 constexpr int kTieMax = 20;       // candidates per near-tie list entry (48 bytes)
+constexpr int kTieChunk = 64;     // near-tie entries an epilogue warp reserves at a time
 constexpr long kWaitLimit = 1L << 22;
 // shared-memory layout (bytes from the 1024-aligned base)
 constexpr int kOffStore = 0;                                  // [128][kPtStride] bytes
 constexpr int kOffSk = kOffStore + kGM * kPtStride;           // [128][kSlots] int16
-constexpr int kOffSmin = kOffSk + kGM * kSlots * 2;           // [128][kSlots] u32
-constexpr int kOffThr = kOffSmin + kGM * kSlots * 4;          // [2][128] u32
+constexpr int kOffThr = kOffSk + kGM * kSlots * 2;            // [2][128] u32
 constexpr int kOffCnt = kOffThr + 2 * kGM * 4;                // [128] int
 constexpr int kOffOver = kOffCnt + kGM * 4;                   // [128] int
 constexpr int kOffStat = kOffOver + kGM * 4;                  // [4] int
@@ -179,30 +179,27 @@ __device__ __forceinline__ double d64row(const float* __restrict__ xrow, const d
 struct EpiSmem {
   unsigned char* store;  // [128][kPtStride]: per slot 16 values, 16 bits each (below)
   short* sk;        // [128][kSlots] first centroid of each stored half
-  uint32_t* smin;   // [128][kSlots] float bits of the half's minimum m
   uint32_t* thr;    // [2][128] shared threshold (float bits), by tile parity
   int* cnt;         // [128] halves allocated
   int* over;        // [128] 1 if a half did not fit
 };
 
 // Keep the 16 values v[0..15] (columns k0..k0+15) of point p; past kSlots
-// halves the point goes to the rescue list.  Every r lies in the binade
-// [1, 2), so bits(r) - bits(m) = (r - m) 2^23 exactly; bits 8..23 of it are
-// stored (r - m in units of 2^-15, truncated): m + q 2^-15 <= r, so no value
-// under the final threshold can test above it.
-__device__ __forceinline__ void store_half(const EpiSmem& s, int p, const unsigned long long* u, int k0, float mn) {
+// halves the point goes to the rescue list.  Each value is kept as bits 8..23
+// of its FP32 pattern (one byte permute per pair): on the binade [1, 2) that
+// holds the screen, q(r) = floor((r - 1) 2^15) + 2^15 is monotone in r, so a
+// value r <= t tests q(r) <= q(t) and no value under the final threshold can
+// be lost (values outside the binade only add candidates, resolved exactly).
+__device__ __forceinline__ void store_half(const EpiSmem& s, int p, const unsigned long long* u, int k0) {
   const int slot = atomicAdd(&s.cnt[p], 1);
   if (slot < kSlots) {
-    const uint32_t bm = __float_as_uint(mn);
     uint32_t w[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      w[q] = __byte_perm((uint32_t)u[q] - bm, (uint32_t)(u[q] >> 32) - bm, 0x6521);
+    for (int q = 0; q < 8; ++q) w[q] = __byte_perm((uint32_t)u[q], (uint32_t)(u[q] >> 32), 0x6521);
     uint4* dst = reinterpret_cast<uint4*>(s.store + p * kPtStride + slot * kHalf * 2);
     dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
     dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
     s.sk[p * kSlots + slot] = (short)k0;
-    s.smin[p * kSlots + slot] = bm;
   } else {
     s.over[p] = 1;
   }
@@ -219,7 +216,6 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
   EpiSmem es;
   es.store = sm + kOffStore;
   es.sk = reinterpret_cast<short*>(sm + kOffSk);
-  es.smin = reinterpret_cast<uint32_t*>(sm + kOffSmin);
   es.thr = reinterpret_cast<uint32_t*>(sm + kOffThr);
   es.cnt = reinterpret_cast<int*>(sm + kOffCnt);
   es.over = reinterpret_cast<int*>(sm + kOffOver);
@@ -249,7 +245,6 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
   }
   if (tid < 4) s_stat[tid] = 0;
   for (int c = tid; c < kpad; c += kGThreads) s_np[c] = a.nprime[c];
-  for (int q = tid; q < kGM * kSlots; q += kGThreads) es.smin[q] = 0u;
   for (int q = tid; q < 2 * kGM; q += kGThreads) es.thr[q] = 0x7f800000u;  // +inf
   for (int q = tid; q < kGM; q += kGThreads) { es.cnt[q] = 0; es.over[q] = 0; }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -336,6 +331,10 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
     }
     int gcount = 0;
     int nflag = 0, nresc = 0;
+    // this warp's reserved near-tie entries [tnext, tend): one global atomic
+    // per kTieChunk entries instead of one per warp and tile (every warp of
+    // the grid adds to the same counter)
+    unsigned tnext = 0, tend = 0;
     // per-point inputs of the next tile are loaded one tile ahead: z and
     // ||x~||^2 for the start estimate (4 threads per point, point tid / 4)
     // and ||x~||^2 for the window (point p)
@@ -440,7 +439,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
           m1 = fminf(x1, hi_f(u[15]));
         };
         auto keep = [&](const unsigned long long* u, int kc, float m) {
-          if (m <= thr) store_half(es, p, u, kc, m);
+          if (m <= thr) store_half(es, p, u, kc);
           thr = fminf(thr, m + delta);
         };
         auto release = [&]() {  // the accumulator may be overwritten
@@ -511,16 +510,15 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
         const int nc = es.cnt[pp];
         const bool over = es.over[pp] != 0;
         const int ns = min(nc, kSlots);
-        // per slot j: the values (16-bit q, see store_half) under the final
-        // threshold t are those with q <= qt_j = (bits(t) - bits(m_j)) / 2^8
+        // the values (16-bit q, see store_half) under the final threshold t
+        // are those with q <= q(t); t past the binade keeps every value
         const uint32_t tb = es.thr[par * kGM + pp];
+        const uint32_t qt = tb >= 0x40000000u ? 0xFFFFu : tb < 0x3F800000u ? 0u : ((tb >> 8) & 0xFFFFu);
+        const uint32_t qt2 = qt | (qt << 16);
         const unsigned char* srow = es.store + pp * kPtStride + sub * 8;
         auto slot_mask = [&](int j) {  // 4 bits: this thread's values of slot j under t
-          const uint32_t bm = es.smin[pp * kSlots + j];
-          if (tb < bm) return 0u;
-          const uint32_t qt = min((tb - bm) >> 8, 0xFFFFu);
           const uint2 w = *reinterpret_cast<const uint2*>(srow + j * kHalf * 2);
-          const uint32_t c0 = __vcmpleu2(w.x, qt | (qt << 16)), c1 = __vcmpleu2(w.y, qt | (qt << 16));
+          const uint32_t c0 = __vcmpleu2(w.x, qt2), c1 = __vcmpleu2(w.y, qt2);
           return (c0 & 1u) | ((c0 >> 15) & 2u) | ((c1 & 1u) << 2) | ((c1 >> 13) & 8u);
         };
         // this thread's 4-bit masks of the point's slots, kept for the
@@ -541,19 +539,29 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
         const bool live = ii < a.n;
         // kind: 1 = decided here, 2 = near tie, 3 = rescue
         const int kind = !live ? 0 : (over || tot == 0 || tot > kTieMax) ? 3 : tot == 1 ? 1 : 2;
-        // list slots, one atomic per warp and list
+        // list slots: near ties from the warp's reserved entries (a new
+        // chunk when they run out; the rest of the old one is used first),
+        // rescues by one atomic per warp (rare)
         const bool lead = sub == 0;
         const unsigned btie = __ballot_sync(0xffffffffu, lead && kind == 2);
         const unsigned bres = __ballot_sync(0xffffffffu, lead && kind == 3);
-        unsigned base_t = 0, base_r = 0;
-        if (lane == 0) {
-          if (btie) base_t = atomicAdd(a.tie_count, (unsigned)__popc(btie));
-          if (bres) base_r = atomicAdd(a.rescue_count, (unsigned)__popc(bres));
+        const unsigned ntie = (unsigned)__popc(btie), rem = tend - tnext, t0 = tnext;
+        unsigned t1 = 0, base_r = 0;
+        if (ntie > rem) {  // warp-uniform
+          if (lane == 0) t1 = atomicAdd(a.tie_count, (unsigned)kTieChunk);
+          t1 = __shfl_sync(0xffffffffu, t1, 0);
+          tnext = t1 + (ntie - rem);
+          tend = t1 + kTieChunk;
+        } else {
+          tnext += ntie;
         }
-        base_t = __shfl_sync(0xffffffffu, base_t, 0);
-        base_r = __shfl_sync(0xffffffffu, base_r, 0);
+        if (bres) {
+          if (lane == 0) base_r = atomicAdd(a.rescue_count, (unsigned)__popc(bres));
+          base_r = __shfl_sync(0xffffffffu, base_r, 0);
+        }
         const unsigned below = (1u << lane) - 1u;
-        const unsigned entry = base_t + __popc(btie & ((1u << (lane & ~3)) - 1u));  // the point's entry
+        const unsigned jt = (unsigned)__popc(btie & ((1u << (lane & ~3)) - 1u));  // the point's rank
+        const unsigned entry = jt < rem ? t0 + jt : t1 + (jt - rem);              // the point's entry
         if ((kind == 1 || kind == 2) && mine > 0) {
           // this thread's candidates: the label (one candidate in all) or
           // its part of the near-tie entry
@@ -582,8 +590,6 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
         // tile (written again only after its first-group barrier)
         __syncwarp();
         if (lead) {
-          // (the slots' minima need no clearing: only slots below the next
-          // tile's count are read, and each of those is written first)
           es.cnt[pp] = 0;
           es.over[pp] = 0;
           es.thr[par * kGM + pp] = 0x7f800000u;  // next used by tile l + 2
@@ -597,6 +603,9 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
       __syncwarp();
       aborted = epi_sync_or(aborted);
     }
+    // unused reserved entries: marked empty (no candidates) for the tie kernel
+    for (unsigned e = tnext + (unsigned)lane; e < tend; e += 32)
+      *reinterpret_cast<int2*>(a.tie_list + 3 * (size_t)e) = make_int2(0, 0);
     if (nflag) atomicAdd(&s_stat[0], nflag);
     if (nresc) atomicAdd(&s_stat[2], nresc);
   }
@@ -630,6 +639,7 @@ __global__ void __launch_bounds__(256) gemm_tie_kernel(GemmArgs a) {
     const int2 h0 = *reinterpret_cast<const int2*>(ent);
     const int64_t ii = h0.x;
     const int nc = h0.y;
+    if (nc == 0) continue;  // an unused reserved entry
     const unsigned short* cl = reinterpret_cast<const unsigned short*>(ent) + 4;
     auto cand = [&](int q) { return (int)cl[q]; };
     const float* xrow = a.xaos + (size_t)ii * kGemmD + sub * 16;
@@ -934,6 +944,12 @@ __global__ void wait_selftest_kernel(int* out) {
 cudaError_t launch_wait_selftest(int* out, cudaStream_t st) {
   wait_selftest_kernel<<<1, 1, 0, st>>>(out);
   return cudaGetLastError();
+}
+
+int64_t gemm_tie_entries(int64_t n, int grid) {
+  // each point at most once, plus the reserved chunks' unused tails (at most
+  // one chunk per epilogue warp)
+  return n + (int64_t)grid * kEpiWarps * kTieChunk;
 }
 
 size_t gemm_smem_bytes(int kpad) {

@@ -166,7 +166,7 @@ struct GemmArgs {
   LoopState* ls;
   int32_t* labels;       // out: labels
   int32_t* rescue_list;  // [N] points resolved over all K by the rescue kernel
-  int4* tie_list;        // [N][3] near ties: point, count, up to 20 16-bit candidates
+  int4* tie_list;        // [gemm_tie_entries][3] near ties: point, count (0: unused), up to 20 16-bit candidates
   unsigned* rescue_count;  // [0] rescue entries, [1] near-tie entries
   unsigned* tie_count;     // = rescue_count + 1
   int64_t n;
@@ -210,6 +210,7 @@ cudaError_t launch_wait_selftest(int* out, cudaStream_t st);
 bool inject_alloc_failure();
 size_t gemm_smem_bytes(int kpad);
 int64_t gemm_xb_rows(int64_t n);
+int64_t gemm_tie_entries(int64_t n, int grid);  // near-tie list capacity (entries of 3 int4)
 int64_t msort_max_chunks(int64_t n, int k);
 cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st);
 
