@@ -144,6 +144,14 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
 }
 __device__ __forceinline__ float lo_f(unsigned long long v) { return __uint_as_float((uint32_t)v); }
 __device__ __forceinline__ float hi_f(unsigned long long v) { return __uint_as_float((uint32_t)(v >> 32)); }
+// minimum of the 16 values in v[0..7] as a tree of depth 3 (eight
+// three-input minima, the same count as a running chain of depth 8)
+__device__ __forceinline__ float min16(const unsigned long long* v) {
+  const float a = fmin3g(lo_f(v[0]), hi_f(v[0]), lo_f(v[1])), b = fmin3g(hi_f(v[1]), lo_f(v[2]), hi_f(v[2]));
+  const float c = fmin3g(lo_f(v[3]), hi_f(v[3]), lo_f(v[4])), d = fmin3g(hi_f(v[4]), lo_f(v[5]), hi_f(v[5]));
+  const float e = fmin3g(lo_f(v[6]), hi_f(v[6]), lo_f(v[7]));
+  return fminf(fmin3g(a, b, c), fmin3g(d, e, hi_f(v[7])));
+}
 // Barrier of the 16 epilogue warps (named barrier 1) that also ORs a flag.
 __device__ __forceinline__ bool epi_sync_or(bool v) {
   uint32_t r;
@@ -429,14 +437,8 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
             u[q] = fma2(u[q], sc2, np.x);
             u[q + 1] = fma2(u[q + 1], sc2, np.y);
           }
-          float x0 = fmin3g(lo_f(u[0]), hi_f(u[0]), lo_f(u[1])), x1 = fmin3g(lo_f(u[8]), hi_f(u[8]), lo_f(u[9]));
-#pragma unroll
-          for (int q = 1; q < 7; ++q) {
-            x0 = fmin3g(x0, hi_f(u[q]), lo_f(u[q + 1]));
-            x1 = fmin3g(x1, hi_f(u[8 + q]), lo_f(u[9 + q]));
-          }
-          m0 = fminf(x0, hi_f(u[7]));
-          m1 = fminf(x1, hi_f(u[15]));
+          m0 = min16(u);
+          m1 = min16(u + 8);
         };
         auto keep = [&](const unsigned long long* u, int kc, float m) {
           if (m <= thr) store_half(es, p, u, kc);
@@ -625,90 +627,113 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_assign_kernel(GemmArgs a) {
 // final threshold): 4 threads per point (16 coordinates each) rank the
 // candidates by the FP32 direct form with its rigorous bound; when that is
 // not conclusive, the first thread decides in FP64 in the oracle's order
-// (lowest index on ties).
-__global__ void __launch_bounds__(256) gemm_tie_kernel(GemmArgs a) {
+// (lowest index on ties).  Each group of 4 threads walks the list with a
+// stride; the next entry is copied into shared memory (cp.async) while the
+// current one is ranked, so the point's row and the first candidates' rows
+// are requested as soon as an entry starts.
+__global__ void __launch_bounds__(256, 4) gemm_tie_kernel(GemmArgs a) {
+  __shared__ __align__(16) int4 s_ent[2][64][3];  // [stage][group] 48-byte entries
   if (a.ls->done) return;
   const unsigned cnt = *a.tie_count;
   const GemmConst gc = *a.gc;
-  const int lane = threadIdx.x & 31, sub = lane & 3;
+  const int lane = threadIdx.x & 31, sub = lane & 3, grp = threadIdx.x >> 2;
   const unsigned gmask = 0xFu << (lane & ~3);
   const unsigned groups = gridDim.x * (blockDim.x / 4);
+  const float sB = sqrtf(gc.B_max);
+  auto fetch = [&](unsigned ee, int st) {  // threads 0..2 of the group copy 16 bytes each
+    if (ee < cnt && sub < 3) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_ent[st][grp][sub]);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(a.tie_list + 3 * (size_t)ee + sub));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
   int n64 = 0;
-  for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) / 4; e < cnt; e += groups) {
-    const int4* ent = a.tie_list + 3 * (size_t)e;
-    const int2 h0 = *reinterpret_cast<const int2*>(ent);
-    const int64_t ii = h0.x;
-    const int nc = h0.y;
-    if (nc == 0) continue;  // an unused reserved entry
-    const unsigned short* cl = reinterpret_cast<const unsigned short*>(ent) + 4;
-    auto cand = [&](int q) { return (int)cl[q]; };
-    const float* xrow = a.xaos + (size_t)ii * kGemmD + sub * 16;
-    float xt[16];
+  unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) / 4;
+  fetch(e, 0);
+  for (int st = 0; e < cnt; e += groups, st ^= 1) {
+    fetch(e + groups, st ^ 1);
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncwarp(gmask);
+    const int4 h = s_ent[st][grp][0];
+    const int nc = h.y;
+    if (nc != 0) {  // 0: an unused reserved entry (the same on the 4 threads)
+      // candidate pairs as 32-bit words of the staged entry
+      const uint32_t* cw = reinterpret_cast<const uint32_t*>(&s_ent[st][grp][0]) + 2;
+      const int64_t ii = h.x;
+      const float* xrow = a.xaos + (size_t)ii * kGemmD + sub * 16;
+      const float A = a.xa[ii];
+      float xt[16];
 #pragma unroll
-    for (int q = 0; q < 16; q += 4) {
-      const float4 xv = *reinterpret_cast<const float4*>(xrow + q);
-      const float4 sv = *reinterpret_cast<const float4*>(a.shift + sub * 16 + q);
-      xt[q] = __fsub_rn(xv.x, sv.x);
-      xt[q + 1] = __fsub_rn(xv.y, sv.y);
-      xt[q + 2] = __fsub_rn(xv.z, sv.z);
-      xt[q + 3] = __fsub_rn(xv.w, sv.w);
-    }
-    float best = 3.0e38f, second = 3.0e38f;
-    int kbest = 0;
-    auto partial = [&](const float4* cr) {  // this thread's 16 coordinates of sum (x~ - c~)^2
-      float part = 0.f;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float4 cv = cr[j];
-        float u = __fsub_rn(xt[4 * j], cv.x); part = __fmaf_rn(u, u, part);
-        u = __fsub_rn(xt[4 * j + 1], cv.y); part = __fmaf_rn(u, u, part);
-        u = __fsub_rn(xt[4 * j + 2], cv.z); part = __fmaf_rn(u, u, part);
-        u = __fsub_rn(xt[4 * j + 3], cv.w); part = __fmaf_rn(u, u, part);
+      for (int q = 0; q < 16; q += 4) {
+        const float4 xv = *reinterpret_cast<const float4*>(xrow + q);
+        const float4 sv = *reinterpret_cast<const float4*>(a.shift + sub * 16 + q);
+        xt[q] = __fsub_rn(xv.x, sv.x);
+        xt[q + 1] = __fsub_rn(xv.y, sv.y);
+        xt[q + 2] = __fsub_rn(xv.z, sv.z);
+        xt[q + 3] = __fsub_rn(xv.w, sv.w);
       }
-      return part;
-    };
-    auto take = [&](int c, float part) {
-      if (part < best || (part == best && c < kbest)) { second = best; best = part; kbest = c; }
-      else if (part < second) second = part;
-    };
-    // two candidates per round (their loads in flight together), taken in
-    // list order; padding columns (c >= K, the same on the 4 threads) skipped
-    for (int q = 0; q < nc; q += 2) {
-      const int c0 = cand(q), c1 = q + 1 < nc ? cand(q + 1) : a.k;
-      const bool v0 = c0 < a.k, v1 = c1 < a.k;
-      float p0 = 0.f, p1 = 0.f;
-      if (v0) p0 = partial(reinterpret_cast<const float4*>(a.ctil + (size_t)c0 * kGemmD + sub * 16));
-      if (v1) p1 = partial(reinterpret_cast<const float4*>(a.ctil + (size_t)c1 * kGemmD + sub * 16));
-      p0 = __fadd_rn(p0, __shfl_xor_sync(gmask, p0, 1));
-      p1 = __fadd_rn(p1, __shfl_xor_sync(gmask, p1, 1));
-      p0 = __fadd_rn(p0, __shfl_xor_sync(gmask, p0, 2));  // identical on the 4 threads
-      p1 = __fadd_rn(p1, __shfl_xor_sync(gmask, p1, 2));
-      if (v0) take(c0, p0);
-      if (v1) take(c1, p1);
-    }
-    int lab = kbest;
-    const float A = a.xa[ii];
-    const float sA = sqrtf(A), sB = sqrtf(gc.B_max), AB = A + gc.B_max;
-    const float e1 = bound64(best, sA, sB, AB), e2 = bound64(second, sA, sB, AB);
-    const float lo2 = second - e2, hi1 = best + e1;
-    const bool need64 = !((lo2 > hi1) && (lo2 - hi1 > gc.tau * (second + e2)));
-    if (sub == 0) {
-      if (need64) {
-        const float* xr = a.xaos + (size_t)ii * kGemmD;
-        double bd = 0.0;
-        int k64 = -1;
-        for (int q = 0; q < nc; ++q) {
-          const int c = cand(q);
-          if (c >= a.k) continue;
-          const double dd = d64row(xr, a.mu + (size_t)c * kGemmD);
-          if (k64 < 0 || dd < bd || (dd == bd && c < k64)) { bd = dd; k64 = c; }
+      float best = 3.0e38f, second = 3.0e38f;
+      int kbest = 0;
+      auto partial = [&](const float4* cr) {  // this thread's 16 coordinates of sum (x~ - c~)^2
+        float part = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 cv = cr[j];
+          float u = __fsub_rn(xt[4 * j], cv.x); part = __fmaf_rn(u, u, part);
+          u = __fsub_rn(xt[4 * j + 1], cv.y); part = __fmaf_rn(u, u, part);
+          u = __fsub_rn(xt[4 * j + 2], cv.z); part = __fmaf_rn(u, u, part);
+          u = __fsub_rn(xt[4 * j + 3], cv.w); part = __fmaf_rn(u, u, part);
         }
-        lab = k64;
-        ++n64;
+        return part;
+      };
+      auto take = [&](int c, float part) {
+        if (part < best || (part == best && c < kbest)) { second = best; best = part; kbest = c; }
+        else if (part < second) second = part;
+      };
+      // two candidates per round (their loads in flight together), taken in
+      // list order; padding columns (c >= K, the same on the 4 threads) skipped
+#pragma unroll
+      for (int q = 0; q < kTieMax; q += 2) {
+        if (q >= nc) break;
+        const int c0 = (int)(cw[q >> 1] & 0xFFFFu), c1 = q + 1 < nc ? (int)(cw[q >> 1] >> 16) : a.k;
+        const bool v0 = c0 < a.k, v1 = c1 < a.k;
+        float p0 = 0.f, p1 = 0.f;
+        if (v0) p0 = partial(reinterpret_cast<const float4*>(a.ctil + (size_t)c0 * kGemmD + sub * 16));
+        if (v1) p1 = partial(reinterpret_cast<const float4*>(a.ctil + (size_t)c1 * kGemmD + sub * 16));
+        p0 = __fadd_rn(p0, __shfl_xor_sync(gmask, p0, 1));
+        p1 = __fadd_rn(p1, __shfl_xor_sync(gmask, p1, 1));
+        p0 = __fadd_rn(p0, __shfl_xor_sync(gmask, p0, 2));  // identical on the 4 threads
+        p1 = __fadd_rn(p1, __shfl_xor_sync(gmask, p1, 2));
+        if (v0) take(c0, p0);
+        if (v1) take(c1, p1);
       }
-      a.labels[ii] = lab;
+      int lab = kbest;
+      const float sA = sqrtf(A), AB = A + gc.B_max;
+      const float e1 = bound64(best, sA, sB, AB), e2 = bound64(second, sA, sB, AB);
+      const float lo2 = second - e2, hi1 = best + e1;
+      const bool need64 = !((lo2 > hi1) && (lo2 - hi1 > gc.tau * (second + e2)));
+      if (sub == 0) {
+        if (need64) {
+          // (rare) the candidates read again from the staged entry
+          const unsigned short* cl = reinterpret_cast<const unsigned short*>(&s_ent[st][grp][0]) + 4;
+          const float* xr = a.xaos + (size_t)ii * kGemmD;
+          double bd = 0.0;
+          int k64 = -1;
+          for (int q = 0; q < nc; ++q) {
+            const int c = cl[q];
+            if (c >= a.k) continue;
+            const double dd = d64row(xr, a.mu + (size_t)c * kGemmD);
+            if (k64 < 0 || dd < bd || (dd == bd && c < k64)) { bd = dd; k64 = c; }
+          }
+          lab = k64;
+          ++n64;
+        }
+        a.labels[ii] = lab;
+      }
     }
+    __syncwarp(gmask);  // stage st is refilled by the next iteration's copy
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (sub == 0 && n64) atomicAdd(&a.ls->fp64_decided, (unsigned long long)n64);
 }
 
