@@ -55,6 +55,9 @@ def parse():
                     help="write the N labels every step, or once after the last step")
     ap.add_argument("--label-bytes", default="auto", choices=["auto", "4", "1"],
                     help="label storage: 1 byte (K <= 256, FP32 paths; the default there) or int32")
+    ap.add_argument("--dist-path", default="auto", choices=["auto", "simt", "tensor"],
+                    help="distance path of the main workload (tensor: the tcgen05 kernels, incl. the TF32 "
+                         "screen of the fused step for d <= 3, K <= 32)")
     ap.add_argument("--tc-operands", default="bf16", choices=["bf16", "f16"],
                     help="operand type of the tensor-core distances (d = 64)")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batch workloads")
@@ -294,7 +297,7 @@ def run_ours(args, ws, rank, local):
     if args.label_bytes == "auto" and (k > 256 or d == 64):
         lb = 4  # 1-byte labels need K <= 256 and the FP32 paths
     g = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy, tc_operands=args.tc_operands,
-                  label_bytes=lb)
+                  label_bytes=lb, dist_path=args.dist_path)
     g.set_points(xt, borrow=True)
     g.set_init(mu0)
     K, W = args.steps, args.warmup
@@ -344,7 +347,7 @@ def run_ours(args, ws, rank, local):
     lab_out = torch.empty(n, dtype=torch.uint8 if lb == 1 else torch.int32).pin_memory()
     e2e_times, phases = [], []
     g2 = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy, tc_operands=args.tc_operands,
-                   label_bytes=lb)
+                   label_bytes=lb, dist_path=args.dist_path)
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -392,7 +395,7 @@ def run_ours(args, ws, rank, local):
     ttc = None
     if args.ttc:
         g3 = km.KMeans(n, d, k, stream=stream, label_policy=args.label_policy, tc_operands=args.tc_operands,
-                       label_bytes=lb)
+                       label_bytes=lb, dist_path=args.dist_path)
         g3.set_points(xt, borrow=True)
         ttc_runs = []
         for rep in range(2):  # the first run also builds the context's step graph
@@ -434,7 +437,7 @@ def run_ours(args, ws, rank, local):
         fp32_peak_tflops = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak_tflops, "traffic": traffic,
-                "kernel": f"assign_fast_kernel<{d}>" if stats["path"] == 1 else "assign_generic_kernel",
+                "kernel": {1: f"assign_fast_kernel<{d}>", 4: f"assign_tcs_kernel<{d}>"}.get(stats["path"], "assign_generic_kernel"),
                 "kernel_ms": assign_ms,
                 "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {mhz:.0f} MHz "
                                f"(sm_max_mhz of {src} peaks); algorithmic 3*N*K*d flops per launch",
@@ -457,7 +460,7 @@ def run_ours(args, ws, rank, local):
            "flagged_per_step": stats["flagged"], "fp64_decided_per_step": stats["fp64_decided"],
            "overflowed_per_step": stats["overflowed"],
            "path": {1: "fused FFMA2", 2: "generic",
-                    3: f"tcgen05 {args.tc_operands.upper()} GEMM-form"}.get(stats["path"]),
+                    3: f"tcgen05 {args.tc_operands.upper()} GEMM-form", 4: "fused, tcgen05 TF32 screen"}.get(stats["path"]),
            "time_to_converge": ttc}
     if args.ttc and args.batch_ttc > 0 and ws == 1:
         out["batch_time_to_converge"] = batch_ttc(args.batch_ttc, dev)
@@ -542,7 +545,8 @@ def extra_workload(km, name, dev, stream, steps=10, warmup=3):
     return {"workload": name, "n": n, "d": d, "k": k, "steps": steps, "warmup": warmup,
             "assign_ms": assign_ms, "ms_per_step": step_ms, "evals_per_s": n * k / (step_ms / 1e3),
             "flagged_per_step": st["flagged"], "fp64_decided_per_step": st["fp64_decided"],
-            "path": {1: "fused FFMA2", 2: "generic", 3: "tcgen05 BF16 GEMM-form"}.get(st["path"]),
+            "path": {1: "fused FFMA2", 2: "generic", 3: "tcgen05 BF16 GEMM-form",
+                     4: "fused, tcgen05 TF32 screen"}.get(st["path"]),
             "roofline": roof}
 
 

@@ -84,7 +84,10 @@ typedef struct km_options {
                            path, whose next step reads the labels */
   int32_t dist_path;    /* KM_DIST_AUTO (default): tensor cores for d = 64 and K <= 1024,
                            else FP32 SIMT; KM_DIST_SIMT: FP32 SIMT kernels always;
-                           KM_DIST_TENSOR: the tcgen05 path or KM_EINVAL */
+                           KM_DIST_TENSOR: a tcgen05 path -- the BF16 GEMM form (d = 64,
+                           K <= 1024) or, for d <= 3 and K <= 32, the fused step with
+                           its screen on TF32 tensor cores (same labels and sums;
+                           slower than the FFMA2 screen at these sizes) -- or KM_EINVAL */
   int32_t tc_operands;  /* operands of the tcgen05 distances: KM_TC_BF16 (default; 8
                            significand bits) or KM_TC_F16 (11 bits, same tensor rate;
                            points and centres scaled by powers of two into FP16's
@@ -238,7 +241,8 @@ typedef struct km_stats {
   int32_t empty_clusters; /* clusters with no points in the last step */
   int64_t overflowed;     /* tensor-core path: points whose candidate list overflowed (all K re-ranked) */
   int32_t path;           /* 1: fused FFMA2 kernel (d <= 4, K <= 256); 2: generic kernel;
-                             3: tcgen05 BF16 GEMM-form kernel (d = 64, K <= 1024) */
+                             3: tcgen05 BF16 GEMM-form kernel (d = 64, K <= 1024);
+                             4: fused kernel with the tcgen05 TF32 screen (d <= 3, K <= 32) */
 } km_stats;
 km_status km_get_stats(km_ctx* ctx, km_stats* out);
 

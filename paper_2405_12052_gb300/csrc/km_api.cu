@@ -49,6 +49,7 @@ struct km_ctx {
   bool own_stream = false;
   int dev = 0, sms = 0;
   bool fast = false;
+  bool tcs = false;  // the fused step screens on the tensor cores (tcgen05 TF32; d <= 3, K <= 32)
   int kpad = 0;
   // points
   float* x_own = nullptr;
@@ -83,7 +84,8 @@ struct km_ctx {
   long long* shard_out = nullptr;  // [k][d+1][2] column totals (host-memory requests)
   long long* shard_in = nullptr;   // [ranks][k][d+1][2] gathered totals (host-memory requests)
   int shard_in_ranks = 0;
-  int path = 0;  // 1 fused (d <= 4, K <= 256), 2 generic, 3 tensor cores (d = 64, K <= 1024)
+  int path = 0;  // 1 fused (d <= 4, K <= 256), 2 generic, 3 tensor cores (d = 64, K <= 1024),
+                 // 4 fused with the tcgen05 TF32 screen (d <= 3, K <= 32)
   // tensor-core path
   void* xb = nullptr;
   float* xa_pt = nullptr;
@@ -210,6 +212,13 @@ cudaError_t launch_assign(km_ctx* c, bool labels_pass = false) {
   if (c->fast) {
     FastArgs a{};
     a.x = c->x; a.ld = c->ld; a.n = c->n; a.k = c->k; a.kpad = c->kpad;
+    if (c->tcs) {
+      a.tab2 = c->tab2; a.ctil = c->ctil4; a.mu = c->mu; a.ic = c->ic; a.dc = c->dc;
+      a.ls = c->ls; a.labels = c->labels; a.labels8 = c->labels8; a.partials = c->partials;
+      a.store_labels = store;
+      a.ignore_done = labels_pass ? 1 : 0;
+      return launch_assign_tcs(c->d, c->G, c->st, a);
+    }
     a.tab2 = c->tab2; a.ctil = c->ctil4; a.mu = c->mu; a.ic = c->ic; a.dc = c->dc;
     a.ls = c->ls; a.labels = c->labels; a.labels8 = c->labels8; a.partials = c->partials;
     a.ntiles = (c->n + kWarpTile - 1) / kWarpTile;
@@ -353,7 +362,14 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
   c->fast = d <= kMaxDFast && k <= kMaxKFast;
   const bool gemm = d == kGemmD && k <= kGemmMaxK && n < (int64_t(1) << 31) &&
                     gemm_smem_bytes((k + 255) / 256 * 256) <= (size_t)p.sharedMemPerBlockOptin;
-  if (c->fast) {
+  // the fused step with its screen on the tensor cores: d <= 3, K <= 32
+  // (one 32-column accumulator per tile; the screen tables are built for
+  // kpad = 32), N < 2^31 (32-bit queue entries)
+  const bool tcs_ok = c->fast && d <= 3 && k <= 32 && n < (int64_t(1) << 31) &&
+                      tcs_smem_bytes() <= (size_t)p.sharedMemPerBlockOptin;
+  c->tcs = tcs_ok && c->opt.dist_path == KM_DIST_TENSOR;  // opt-in: the FFMA2 screen is faster here
+  if (c->tcs) c->kpad = 32;
+  if (c->fast && !c->tcs) {
     // one 32-bit sum window per half-warp (double-buffered points) when it
     // fits with as many resident blocks per SM as one window per warp
     // (single-buffered points) allows, else the smaller layout
@@ -372,14 +388,21 @@ km_status km_create(km_ctx** out, int64_t n, int32_t d, int32_t k, const km_opti
     }
   }
   const int64_t ntiles = (n + kWarpTile - 1) / kWarpTile;  // warp-tiles of 256 points
-  if (c->opt.dist_path == KM_DIST_TENSOR && !gemm)
-    return fail(c, KM_EINVAL, "tensor-core distances need d = 64, K <= 1024 and N < 2^31");
-  c->path = c->opt.dist_path == KM_DIST_TENSOR ? 3 : (c->fast ? 1 : ((gemm && c->opt.dist_path == KM_DIST_AUTO) ? 3 : 2));
+  if (c->opt.dist_path == KM_DIST_TENSOR && !gemm && !c->tcs)
+    return fail(c, KM_EINVAL, "tensor-core distances need d <= 3 and K <= 32, or d = 64 and K <= 1024 (N < 2^31)");
+  c->path = c->tcs ? 4
+                   : c->opt.dist_path == KM_DIST_TENSOR ? 3
+                                                        : (c->fast ? 1 : ((gemm && c->opt.dist_path == KM_DIST_AUTO) ? 3 : 2));
   if (c->path == 3 && c->opt.label_bytes == 1)
     return fail(c, KM_EINVAL, "1-byte labels are for the FP32 paths (the tensor-core path reads int32 labels)");
   if (c->path == 3) {
     c->kpad = (k + 255) / 256 * 256;
     c->G = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, c->sms));
+  } else if (c->tcs) {
+    // one CTA per SM (the whole TMEM); at most 4 x 1023 super-tiles of 256
+    // points per CTA so that the int64 block totals stay in range
+    const int64_t U = (n + 255) / 256;
+    c->G = (int)std::max<int64_t>(tcs_grid(n, c->sms), (U + 4 * 1023 - 1) / (4 * 1023));
   } else if (c->fast) {
     // one resident wave; each warp strides over warp-tiles, and no block
     // takes more than 2^19 points (int64 per-block sums stay in range)

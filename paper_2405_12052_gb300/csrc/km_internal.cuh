@@ -210,6 +210,10 @@ cudaError_t launch_wait_selftest(int* out, cudaStream_t st);
 bool inject_alloc_failure();
 size_t gemm_smem_bytes(int kpad);
 int64_t gemm_xb_rows(int64_t n);
+// fused step with the tcgen05 TF32 screen (d <= 3, K <= 32; the screen tables built for kpad = 32)
+size_t tcs_smem_bytes();
+int tcs_grid(int64_t n, int sms);
+cudaError_t launch_assign_tcs(int d, int grid, cudaStream_t st, const FastArgs& a);
 int64_t gemm_tie_entries(int64_t n, int grid);  // near-tie list capacity (entries of 3 int4)
 int64_t msort_max_chunks(int64_t n, int k);
 cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st);

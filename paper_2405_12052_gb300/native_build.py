@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libkm.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["km_assign.cu", "km_update.cu", "km_api.cu", "km_noalloc.cu", "km_gemm.cu", "km_msort.cu",
+SOURCES = ["km_assign.cu", "km_assign_tc.cu", "km_update.cu", "km_api.cu", "km_noalloc.cu", "km_gemm.cu", "km_msort.cu",
            "km_batch.cu", "km_batch_api.cu", "km_kpp.cu",
            "km_setnet.cu", "km_setnet_api.cu", "km_objective.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -306,8 +306,8 @@ def test_label_policy_final_step_api(km, oracle):
 
 def test_dist_path_option(km, oracle):
     """dist_path: "simt" keeps d = 64 off the tensor cores (generic FP32
-    path, same bit-exact labels); "tensor" on a shape the tcgen05 path does
-    not take is an argument error; "tensor" on d = 64 selects it."""
+    path, same bit-exact labels); "tensor" on a shape no tcgen05 path
+    takes is an argument error; "tensor" on d = 64 selects the GEMM form."""
     x, _, _ = synth.iso_mixture(20_000, 64, 40, sigma=1.0, box=8.0, seed=51)
     mu0, _ = synth.init_distinct(x, 100, seed=52)
     st = lockstep(km, oracle, x, mu0, steps=1, dist_path="simt")
@@ -316,8 +316,10 @@ def test_dist_path_option(km, oracle):
     assert g.stats()["path"] == 3
     g.close()
     with pytest.raises(km.KMError) as ei:
-        km.KMeans(1000, 3, 8, dist_path="tensor")
+        km.KMeans(1000, 3, 40, dist_path="tensor")  # neither d = 64 nor d <= 3 with K <= 32
     assert ei.value.status == -1
+    with pytest.raises(km.KMError):
+        km.KMeans(1000, 4, 8, dist_path="tensor")
 
 
 def test_run_logged_records_every_step(km, oracle):
