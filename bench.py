@@ -167,8 +167,8 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {
-    "assign_fast_kernel<3>": ("km_assign.cu", "km_internal.cuh"),
-    "gemm_assign_kernel": ("km_gemm.cu", "km_internal.cuh"),
+    "assign_fast_kernel<3>": ("km_assign.cu", "km_fast_common.cuh", "km_internal.cuh"),
+    "gemm_assign_kernel": ("km_gemm.cu", "km_tcgen05.cuh", "km_internal.cuh"),
 }
 
 
