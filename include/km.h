@@ -330,12 +330,12 @@ km_status km_batch_set_init(km_batch* b, const double* mu0);
  * km_batch_run does this when it was not called): the batch kernel's tile
  * sizes (512, 1024 points) x block sizes (128, 256, 512 threads), then the
  * fused kernel's tile machinery (8 points per lane, 256 threads) on tiles of
- * 2048 and 8192 points.  Every shape gives the same results.  Leaves
+ * 8192 and 32768 points.  Every shape gives the same results.  Leaves
  * centroids and iteration counts unchanged.  Outputs may be NULL. */
 km_status km_batch_tune(km_batch* b, int32_t* tile_out, int32_t* threads_out);
 
 /* Use a launch shape without timing (one the tuner times: tile_points 512 or
- * 1024 with threads 128, 256 or 512, or tile_points 2048 or 8192 with 256
+ * 1024 with threads 128, 256 or 512, or tile_points 8192 or 32768 with 256
  * threads for the fused kernel), e.g. a shape a previous km_batch_tune chose
  * for the same instances, kept in a cache.  Errors: KM_EINVAL (another
  * shape), KM_ESTATE (no points). */
@@ -369,7 +369,7 @@ typedef struct km_batch_info {
   int32_t tiles;
   int32_t tuned;          /* 1 once km_batch_tune ran */
   int32_t tune_candidates;
-  float tune_ms[8];       /* per candidate: 512 x {128,256,512}, 1024 x {...}, then 2048 and 8192 (fused) */
+  float tune_ms[8];       /* per candidate: 512 x {128,256,512}, 1024 x {...}, then 8192 and 32768 (fused) */
 } km_batch_info;
 km_status km_batch_get_info(km_batch* b, km_batch_info* out);
 

@@ -58,7 +58,7 @@ namespace {
 constexpr int kTileCand[2] = {512, 1024};
 constexpr int kThreadCand[3] = {128, 256, 512};
 // the fused kernel's tiles (a multiple of its 256-point warp-tiles; 256 threads)
-constexpr int kFastTileCand[2] = {2048, 8192};
+constexpr int kFastTileCand[2] = {8192, 32768};
 constexpr int kGraphSteps = 4;
 
 km_status bfail(km_batch* b, km_status s, const std::string& m) {

@@ -47,15 +47,15 @@ def test_batch_matches_oracle_per_instance(km, oracle):
     r = b.run(100, 1e-6)
     _check_against_oracle(b, insts, r, oracle, 100, 1e-6)
     info = b.info()
-    assert info["tuned"] == 1 and info["tile_points"] in (512, 1024, 2048, 8192) and info["tune_candidates"] == 8
+    assert info["tuned"] == 1 and info["tile_points"] in (512, 1024, 8192, 32768) and info["tune_candidates"] == 8
     b.close()
 
 
-@pytest.mark.parametrize("shape", [(512, 128), (1024, 512), (2048, 256), (8192, 256)])
+@pytest.mark.parametrize("shape", [(512, 128), (1024, 512), (8192, 256), (32768, 256)])
 def test_batch_every_shape_matches_oracle(km, oracle, shape):
     """Every launch shape the tuner times gives the oracle's results: the
     batch kernel's tiles, and the fused kernel's tile machinery (tiles of
-    2048 and 8192 points: instances of d = 1, 2 and 3 following one another
+    8192 and 32768 points: instances of d = 1, 2 and 3 following one another
     in a block, partial tiles, rows not 16-byte aligned in the packed
     layout, labels at odd offsets)."""
     insts = synth.batch_instances(40, seed=15, n_lo=300, n_hi=30_000)
