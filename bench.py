@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--tc-operands", default="bf16", choices=["bf16", "f16"],
                     help="operand type of the tensor-core distances (d = 64)")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batch workloads")
+    ap.add_argument("--batch-shape", default=None,
+                    help="TILExTHREADS: the batch workload's launch shape, fixed instead of tuned")
     ap.add_argument("--learned-count", type=int, default=6, help="held-out mixtures of the learned-init workload")
     ap.add_argument("--no-ttc", dest="ttc", action="store_false",
                     help="skip the time-to-converge records of the default line")
@@ -652,7 +654,11 @@ def run_batch(args, ws, rank, local):
     b.set_init(mus)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    tile, thr = b.tune()
+    if args.batch_shape:  # a fixed launch shape (e.g. for a profile of one kernel), no tuner
+        tile, thr = (int(v) for v in args.batch_shape.split("x"))
+        b.set_shape(tile, thr)
+    else:
+        tile, thr = b.tune()
     tune_s = time.perf_counter() - t0
     clocks = ClockSampler(local)
     clocks.start()
@@ -692,7 +698,8 @@ def run_batch(args, ws, rank, local):
     if assign_ms:
         ach = flops / (assign_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                "traffic": None, "kernel": "batch_assign_kernel", "kernel_ms": assign_ms,
+                "traffic": None, "kernel": "batch_fast_kernel" if tile > 1024 else "batch_assign_kernel",
+                "kernel_ms": assign_ms,
                 "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x sm_max_mhz ({src} peaks); "
                                "algorithmic sum_i 3 N_i K_i d_i flops per launch with every instance active"}
     # plain km_run, one instance after another
