@@ -936,7 +936,9 @@ cudaError_t launch_gemm_assign(int grid, cudaStream_t st, const GemmArgs& a) {
   gemm_assign_kernel<<<grid, kGThreads, smem, st>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  gemm_tie_kernel<<<grid * 8, 256, 0, st>>>(a);
+  // one resident wave (4 blocks of 256 threads per SM at 64 registers); each
+  // group of 4 threads strides over the list
+  gemm_tie_kernel<<<grid * 4, 256, 0, st>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   gemm_rescue_kernel<<<grid * 4, 256, 0, st>>>(a);
