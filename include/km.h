@@ -196,8 +196,10 @@ km_status km_sync(km_ctx* ctx, int32_t* iters_out, double* e_out, int32_t* done_
  *
  * mem: KM_HOST (host arrays; the call synchronizes) or KM_DEVICE_COPY
  * (device arrays of the context's device, used on the context's stream
- * without synchronizing).  The FP32 paths only (KM_EINVAL on the
- * tensor-core path).  km_set_grid_exponent returns KM_EINVAL below the
+ * without synchronizing).  Every path: on the tensor-core GEMM path the
+ * totals come from its sorted mean calculation (each cluster's chunk sums
+ * added in order), with the same table layout.  km_set_grid_exponent
+ * returns KM_EINVAL below the
  * exponent the shard's own points need or above 100, KM_ESTATE before
  * km_set_points. */
 km_status km_grid_exponent(km_ctx* ctx, int32_t* ex_out);

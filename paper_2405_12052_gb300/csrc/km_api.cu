@@ -825,14 +825,16 @@ km_status km_shard_totals(km_ctx* c, int64_t* out, int32_t mem) {
   km_status s = ready(c);
   if (s != KM_OK) return s;
   if (!out || (mem != KM_HOST && mem != KM_DEVICE_COPY)) return fail(c, KM_EINVAL, "bad output");
-  if (c->path == 3) return fail(c, KM_EINVAL, "sharded steps are for the FP32 paths (d <= 4 or any d off the tensor cores)");
   const size_t words = (size_t)c->k * (c->d + 1) * 2;
   long long* dst = reinterpret_cast<long long*>(out);
   if (mem == KM_HOST) {
     if (!c->shard_out) KM_CUDA(c, dalloc(&c->shard_out, words));
     dst = c->shard_out;
   }
-  KM_CUDA(c, launch_shard_totals(c->st, update_args(c), dst));
+  // the tensor-core path sums by the sorted mean calculation; the FP32 paths
+  // add their per-block partials
+  KM_CUDA(c, c->path == 3 ? launch_msort_shard_totals(msort_args(c), dst, c->st)
+                          : launch_shard_totals(c->st, update_args(c), dst));
   if (mem == KM_HOST) {
     KM_CUDA(c, cudaMemcpyAsync(out, dst, words * sizeof(long long), cudaMemcpyDeviceToHost, c->st));
     KM_CUDA(c, cudaStreamSynchronize(c->st));
@@ -844,7 +846,6 @@ km_status km_shard_update(km_ctx* c, const int64_t* tables, int32_t ranks, int32
   km_status s = ready(c);
   if (s != KM_OK) return s;
   if (!tables || ranks < 1 || (mem != KM_HOST && mem != KM_DEVICE_COPY)) return fail(c, KM_EINVAL, "bad tables");
-  if (c->path == 3) return fail(c, KM_EINVAL, "sharded steps are for the FP32 paths (d <= 4 or any d off the tensor cores)");
   const size_t words = (size_t)c->k * (c->d + 1) * 2;
   const long long* src = reinterpret_cast<const long long*>(tables);
   if (mem == KM_HOST) {
@@ -858,7 +859,12 @@ km_status km_shard_update(km_ctx* c, const int64_t* tables, int32_t ranks, int32
     KM_CUDA(c, cudaMemcpyAsync(c->shard_in, tables, words * ranks * sizeof(long long), cudaMemcpyHostToDevice, c->st));
     src = c->shard_in;
   }
-  KM_CUDA(c, launch_shard_update(c->st, update_args(c), src, ranks));
+  if (c->path == 3) {
+    KM_CUDA(c, launch_msort_shard_update(msort_args(c), src, ranks, c->st));
+    KM_CUDA(c, launch_gemm_prepare(c->st, gemm_prep_args(c)));  // the next step's tables
+  } else {
+    KM_CUDA(c, launch_shard_update(c->st, update_args(c), src, ranks));
+  }
   if (mem == KM_HOST) KM_CUDA(c, cudaStreamSynchronize(c->st));  // the host tables may be reused at once
   return KM_OK;
 }

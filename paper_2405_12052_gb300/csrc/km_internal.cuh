@@ -217,6 +217,10 @@ cudaError_t launch_assign_tcs(int d, int grid, cudaStream_t st, const FastArgs& 
 int64_t gemm_tie_entries(int64_t n, int grid);  // near-tie list capacity (entries of 3 int4)
 int64_t msort_max_chunks(int64_t n, int k);
 cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st);
+// sharded steps on the tensor-core path: the context's int128 column totals
+// ([k][d+1] of low, high word), and the update from the ranks' tables
+cudaError_t launch_msort_shard_totals(const MsortArgs& a, long long* out, cudaStream_t st);
+cudaError_t launch_msort_shard_update(const MsortArgs& a, const long long* tables, int ranks, cudaStream_t st);
 
 // ---- batched instances (d <= 3, K <= 64) ----
 constexpr int kBatchMaxK = 64;

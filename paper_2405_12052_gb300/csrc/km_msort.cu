@@ -308,11 +308,102 @@ __global__ void __launch_bounds__(1024) ms_close_kernel(const double* df2, int k
   }
 }
 
+// Sharded steps: the cluster's exact int128 coordinate totals (its chunk
+// sums added in chunk order, as the finalize kernel does) and its count, in
+// the sharded-step table layout [k][d+1] of (low word, high word).
+__global__ void __launch_bounds__(256) ms_shard_totals_kernel(const unsigned long long* counts, const int* cfirst,
+                                                              const long long* chunk_sums, int k, int d,
+                                                              long long* out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= k * (d + 1)) return;
+  const int c = q / (d + 1), j = q - c * (d + 1);
+  const long long cnt = (long long)counts[c];
+  unsigned long long lo = 0ull;
+  long long hi = 0ll;
+  if (j == d) {
+    lo = (unsigned long long)cnt;
+  } else {
+    const long long first = cfirst[c];
+    const int nch = (int)((cnt + kChunk - 1) / kChunk);
+    for (int t = 0; t < nch; ++t) {
+      const long long v = chunk_sums[(size_t)(first + t) * d + j];
+      const unsigned long long nl = lo + (unsigned long long)v;
+      hi += (v < 0 ? -1ll : 0ll) + (nl < lo ? 1ll : 0ll);
+      lo = nl;
+    }
+  }
+  out[(size_t)q * 2] = (long long)lo;
+  out[(size_t)q * 2 + 1] = hi;
+}
+
+// Sharded steps: the ranks' tables added in rank order (int128), then the
+// finalize kernel's conversion and divide -- the same integers as one
+// context over all points, so the same centroids.
+__global__ void __launch_bounds__(256) ms_shard_finalize_kernel(const long long* tables, int ranks, int k, int d,
+                                                                const DataConst* dcp, double* mu,
+                                                                long long* counts_out, double* df2,
+                                                                const LoopState* ls) {
+  if (ls->done) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= k * d) return;
+  const int c = q / d, j = q - c * d;
+  const size_t cols = (size_t)k * (d + 1);
+  const size_t col = (size_t)c * (d + 1) + j, ccol = (size_t)c * (d + 1) + d;
+  unsigned long long lo = 0ull, clo = 0ull;
+  long long hi = 0ll, chi = 0ll;
+  for (int r = 0; r < ranks; ++r) {
+    const long long* t = tables + (size_t)r * cols * 2;
+    const unsigned long long vl = (unsigned long long)t[col * 2];
+    const unsigned long long nl = lo + vl;
+    hi += t[col * 2 + 1] + (nl < lo ? 1ll : 0ll);
+    lo = nl;
+    const unsigned long long cl = (unsigned long long)t[ccol * 2];
+    const unsigned long long ncl = clo + cl;
+    chi += t[ccol * 2 + 1] + (ncl < clo ? 1ll : 0ll);
+    clo = ncl;
+  }
+  const long long cnt = (long long)clo;  // counts fit in 64 bits
+  const double old = mu[q];
+  double nw = old;
+  if (cnt > 0) nw = __ddiv_rn(ldexp(ms_i128_to_double(lo, hi), dcp->G0), (double)cnt);
+  const double df = __dsub_rn(nw, old);
+  df2[q] = __dmul_rn(df, df);
+  mu[q] = nw;
+  if (j == 0) counts_out[c] = cnt;
+}
+
 }  // namespace
 
 int64_t msort_max_chunks(int64_t n, int k) { return n / kChunk + k + 1; }
 
+static cudaError_t msort_sums(const MsortArgs& a, cudaStream_t st);
+
 cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st) {
+  cudaError_t e = msort_sums(a, st);
+  if (e != cudaSuccess) return e;
+  ms_finalize_kernel<<<(a.k * a.d + 255) / 256, 256, 0, st>>>(a.counts_u, a.cfirst, a.chunk_sums, a.k, a.d, a.dc,
+                                                              a.mu, a.counts, a.df2, a.ls);
+  ms_close_kernel<<<1, 1024, 0, st>>>(a.df2, a.k * a.d, a.counts, a.k, a.ls);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_msort_shard_totals(const MsortArgs& a, long long* out, cudaStream_t st) {
+  cudaError_t e = msort_sums(a, st);
+  if (e != cudaSuccess) return e;
+  ms_shard_totals_kernel<<<(a.k * (a.d + 1) + 255) / 256, 256, 0, st>>>(a.counts_u, a.cfirst, a.chunk_sums, a.k,
+                                                                        a.d, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_msort_shard_update(const MsortArgs& a, const long long* tables, int ranks, cudaStream_t st) {
+  ms_shard_finalize_kernel<<<(a.k * a.d + 255) / 256, 256, 0, st>>>(tables, ranks, a.k, a.d, a.dc, a.mu, a.counts,
+                                                                    a.df2, a.ls);
+  ms_close_kernel<<<1, 1024, 0, st>>>(a.df2, a.k * a.d, a.counts, a.k, a.ls);
+  return cudaGetLastError();
+}
+
+// Histogram, scan, scatter and chunk sums of the sorted mean calculation.
+static cudaError_t msort_sums(const MsortArgs& a, cudaStream_t st) {
   // callers skip the whole step once the loop has stopped: the flag is read
   // by the finalize kernel only, so the earlier kernels run unconditionally
   cudaError_t e = cudaMemsetAsync(a.counts_u, 0, sizeof(unsigned long long) * a.k, st);
@@ -340,9 +431,6 @@ cudaError_t launch_msort_step(const MsortArgs& a, cudaStream_t st) {
     ms_chunk_sum_kernel<<<(unsigned)a.max_chunks, threads, sizeof(long long) * (size_t)std::max(1, threads / a.d) * a.d,
                           st>>>(a.xa, a.d, a.perm, a.chunks, a.nchunks, a.dc, a.chunk_sums);
   }
-  ms_finalize_kernel<<<(a.k * a.d + 255) / 256, 256, 0, st>>>(a.counts_u, a.cfirst, a.chunk_sums, a.k, a.d, a.dc,
-                                                              a.mu, a.counts, a.df2, a.ls);
-  ms_close_kernel<<<1, 1024, 0, st>>>(a.df2, a.k * a.d, a.counts, a.k, a.ls);
   return cudaGetLastError();
 }
 

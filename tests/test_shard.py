@@ -8,7 +8,8 @@ divides, section "Parallel Lloyd's algorithm", with an all-gather).
   host tensors): a ragged split of the points, several steps; every shard's
   centroids, counts and E bit-identical to one context over all points, its
   labels equal to that context's labels of its points, and the whole equal to
-  the FP64 oracle.
+  the FP64 oracle -- on the fused FP32 path (d = 3) and on the tensor-core
+  GEMM path (d = 64, totals from the sorted mean calculation).
 """
 import os
 import socket
@@ -155,4 +156,55 @@ def test_sharded_steps_equal_one_context(oracle):
             assert np.array_equal(cr, c), (r, t)      # bit-identical centroids
             assert np.array_equal(cntr, cnt), (r, t)  # global counts
             assert er == e, (r, t)                    # bit-identical E
+    g.close()
+
+
+@pytest.mark.gpu
+def test_sharded_steps_tensor_core_path(oracle):
+    """The same on the tensor-core GEMM path (d = 64): each shard's totals
+    come from its sorted mean calculation; centroids, counts and E equal one
+    context's bit for bit, labels that context's labels of its points."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2405_12052_gb300 as km
+    import synth
+    km.build()
+    x, _, _ = synth.iso_mixture(60_013, 64, 24, sigma=1.0, box=8.0, seed=43)
+    k = 64
+    mu0, _ = synth.init_distinct(x, k, seed=44)
+    order = np.argsort(x[0], kind="stable")
+    x = np.ascontiguousarray(x[:, order])
+    n = x.shape[1]
+    split = [0, int(0.4 * n), n]
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_gpu_rank, args=(r, 2, port, x, mu0, split, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    g = km.KMeans(n, 64, k)
+    g.set_points(x)
+    g.set_init(mu0)
+    assert g.stats()["path"] == 3
+    ref_ex = g.grid_exponent()
+    mu = mu0
+    for t in range(STEPS):
+        e, _ = g.step()
+        z, c, cnt = g.labels(), g.centroids(), g.counts()
+        zo, mo, co, _ = oracle.step(x, mu)
+        assert np.array_equal(z, zo) and np.array_equal(cnt, co)
+        mu = c
+        for r in range(2):
+            ex_local, ex, recs = out[r]
+            assert ex == ref_ex and ex_local <= ex
+            zr, cr, cntr, er, it = recs[t]
+            assert it == t + 1
+            assert np.array_equal(zr, z[split[r]:split[r + 1]]), (r, t)
+            assert np.array_equal(cr, c), (r, t)
+            assert np.array_equal(cntr, cnt), (r, t)
+            assert er == e, (r, t)
     g.close()
