@@ -21,10 +21,11 @@
 //                                                    xl.al omitted
 // with sum_j |x~_j a_kj| <= 2^sigma (||x~||^2 + B_max) and |n| < 2^(eM+1):
 // 32 ulps of the binade plus 40.2 2^-23 G (A + B_max) ulps, added to the flag
-// threshold (constant part and per unit of A = ||x~||^2).  Everything after the screen -- group minima packed
-// with the group index, running top-2, exact FP32-chain recompute of the
-// winning group, flag test in units of the binade, per-warp queue and FP32 /
-// FP64 re-check, exact integer sums -- is the FFMA2 kernel's.
+// threshold (constant part and per unit of A = ||x~||^2).  Everything after
+// the screen -- group minima packed with the group index, running top-2,
+// exact FP32-chain recompute of the winning group, flag test in units of the
+// binade, per-warp queue and FP32 / FP64 re-check, exact integer sums -- is
+// the FFMA2 kernel's.
 //
 // CTA: 16 warps in 4 quads; a quad (warps 4q .. 4q+3, TMEM lane quarters
 // 0..3) owns 256-point super-tiles (two MMA tiles of 128 points), two stages
