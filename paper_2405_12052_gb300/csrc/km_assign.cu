@@ -38,7 +38,7 @@ struct FastSmem {
   float4* ctil;             // [k] fp32 centroids for the re-check (block; two-window layout only, else global)
   float* xbuf;              // [kWarps][nbuf][D][kWarpTile] points (double-buffered when nbuf = 2)
   uint32_t* queue;          // [kWarps][kWarpQueue] flagged points
-  uint32_t* win;            // [kWarps][nwin][k+1][WIN] 32-bit windows (per half-warp when nwin = 2); bin k discards
+  uint32_t* win;            // [kWarps][nwin][k+1][WIN] 32-bit windows (per 8 lanes when nwin = 4, per half-warp when 2); bin k discards
   int* cnt;                 // [2]: flagged, fp64-decided (block totals)
   FastSmem() = default;
   __device__ FastSmem(unsigned char* sm, int kpad, int k, int nwin, int nbuf) {
@@ -89,14 +89,14 @@ __device__ __forceinline__ void prefetch_tile(const FastArgs& a, float* xb, int6
 }
 
 // Re-decide the points in this warp's queue (warp-level: lanes take
-// entries; windows are flushed every 32 rounds with two windows per warp, 16
-// with one: <= 512 additions per bin).
+// entries; windows are flushed every 64 rounds with four windows per warp,
+// 32 with two, 16 with one: <= 512 additions per bin).
 template <int D>
 __device__ void drain_warp_queue(const FastArgs& a, FastSmem<D>& sm, uint32_t* q, int qn, int wid,
                                  int wtot, uint32_t* wwarp, uint32_t* wmine, long long* acc, int lane,
                                  const float* s, const DataConst& dc, float B_max, float tau, int& n64) {
   flush_windows<D>(wwarp, acc, a.k, a.nwin, lane, dc.bits_C_hi, dc.bits_C_lo);
-  const int rmask = a.nwin == 2 ? 31 : 15;
+  const int rmask = a.nwin == 4 ? 63 : a.nwin == 2 ? 31 : 15;
   for (int r = 0, b = 0; b < qn; ++r, b += 32) {
     const int e = b + lane;
     if (e < qn) {
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
 
   const int nwin = a.nwin;
   uint32_t* wwarp = sm.win + (size_t)warp * nwin * (k + 1) * WIN;
-  uint32_t* wmine = wwarp + (size_t)(nwin == 2 ? (lane >> 4) : 0) * (k + 1) * WIN;
+  uint32_t* wmine = wwarp + (size_t)(nwin == 4 ? (lane >> 3) : nwin == 2 ? (lane >> 4) : 0) * (k + 1) * WIN;
   long long* acc = sm.acc;
   uint32_t* q = sm.queue + (size_t)warp * kWarpQueue;
   float* xb = sm.xbuf + (size_t)warp * nbuf * D * kWarpTile;
@@ -501,8 +501,8 @@ __global__ void __launch_bounds__(kThreads, KM_MINB) assign_fast_kernel(FastArgs
     else
       process_tile<D, KG, CT, false>(a, sm, cx, s2, xcur, base, m, lane, wmine, q, qn);
     if (nbuf == 1 && tile + wtot < ntiles) prefetch_tile<D>(a, xb, (int64_t)(tile + wtot) * kWarpTile, lane);
-    // 16 lanes x 8 points x 4 tiles (or 32 lanes x 8 points x 2 tiles): <= 512 additions per bin
-    if (++since_flush == (nwin == 2 ? 4 : 2)) {
+    // 8 lanes x 8 points x 8 tiles, 16 x 8 x 4 or 32 x 8 x 2: <= 512 additions per bin
+    if (++since_flush == (nwin == 4 ? 8 : nwin == 2 ? 4 : 2)) {
       flush_windows<D>(wwarp, acc, k, nwin, lane, dc.bits_C_hi, dc.bits_C_lo);
       since_flush = 0;
     }

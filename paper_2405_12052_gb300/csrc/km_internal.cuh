@@ -112,7 +112,7 @@ struct FastArgs {
   int32_t* labels;
   long long* partials;             // [gridDim.x][k][D+1]
   int64_t ntiles;
-  int nwin;                        // 32-bit sum windows per warp: 2 (one per half-warp) or 1 (large K)
+  int nwin;                        // 32-bit sum windows per warp: 4 (one per 8 lanes), 2 (one per half-warp) or 1 (large K)
   int store_labels;                // 0: labels are not written (label policy "final")
   uint8_t* labels8;                // non-null: labels are written here as bytes (K <= 256), not to labels
   int ignore_done;                 // 1: run even after the stop flag (the final labels pass)
